@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Throughput of the batched A-MMMSE solver on GB300.
+
+Workload (one "step"): the single-cell P-sweep batch -- Nt=64 BS antennas,
+K=16 users, Nr=4 receive antennas, d=4 streams, i.i.d. CN(0,1) channels,
+sigma^2=1, alpha~U(0.5,1.5), P = 0..30 dB in 5 dB steps x 1024 realizations
+= 7168 instances -- solved end to end: initial projection, 50 iterations of
+Algorithm 3 (two-stage warm start included) and the FP64 WSR evaluation.
+Metric: instance-solves/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32]
+    python bench.py --impl reference      # the FP64 CPU oracle on host cores
+
+Under torchrun every rank solves its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "instance-solves/s at <=1e-3 WSR gap to FP64 oracle vs plain path; % roofline"
+UNIT = "instance-solves/s"
+ITERS = 50
+N_PER_P = 1024
+WORKLOAD = "single-cell P sweep: Nt=64, K=16, Nr=4, d=4, iid CN(0,1), P=0..30 dB (7x1024 instances), 50 iterations"
+
+
+def algorithmic_gemm_flops(C, K, Nt, Nr, d):
+    """Flops of the two complex GEMMs of one iteration of one instance:
+    Z = H V and G = H^H Y, each (C K Nr) x Nt x (K d) per cell, 8 real
+    flops per complex multiply-add."""
+    m, n = C * K * Nr, K * d
+    return 2 * 8 * m * Nt * n * C
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _oracle_worker(args):
+    first, count, iters = args
+    import workloads as wl
+    from oracle import solvers as osv
+    from oracle import model as om
+    out = []
+    for inst in wl.single_cell_64(N_PER_P, first=first, count=count):
+        V0 = osv.initial_precoder(inst.G0, inst.P)
+        r = osv.ammmse(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0, iters)
+        out.append(om.wsr_bits(inst.H, r.V, inst.sigma2, inst.alpha, inst.K, inst.Nr, inst.d))
+    return out
+
+
+def make_pool(cores):
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    return mp.get_context("spawn").Pool(cores)
+
+
+def oracle_throughput(pool, cores, n_instances, offset=0):
+    """Solve n_instances of the workload with the oracle over the pool;
+    returns (instance-solves/s, seconds)."""
+    per = max(1, n_instances // cores)
+    jobs = []
+    total = 0
+    b = offset
+    while total < n_instances:
+        c = min(per, n_instances - total)
+        jobs.append(((b % (7 * N_PER_P)), min(c, 7 * N_PER_P - (b % (7 * N_PER_P))), ITERS))
+        total += jobs[-1][1]
+        b += jobs[-1][1]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, jobs)
+    dt = time.perf_counter() - t0
+    n = sum(len(r) for r in res)
+    return n / dt, dt, n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    pool = make_pool(cores)
+    # warm-up (imports in the workers)
+    oracle_throughput(pool, cores, cores)
+    vals, n_total, t_total = [], 0, 0.0
+    per_step = max(cores, 2 * cores)
+    for s in range(args.warmup):
+        oracle_throughput(pool, cores, per_step, offset=s * per_step)
+    for s in range(args.steps):
+        v, dt, n = oracle_throughput(pool, cores, per_step, offset=(args.warmup + s) * per_step)
+        vals.append(v)
+        n_total += n
+        t_total += dt
+    pool.close()
+    value = n_total / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_step": per_step, "iterations": ITERS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} instances per step of the same workload, numpy float64 oracle, "
+                                   f"one process per core"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = make_pool(cores)  # spawned before the first CUDA call
+
+    import torch
+    import workloads as wl
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2510_20507_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    dev = torch.device("cuda", local)
+
+    # inputs of this rank (rank r uses a disjoint seed range)
+    insts = wl.single_cell_64(N_PER_P, base_seed=2 + 1000 * rank)
+    pk = wl.pack(insts)
+    batch = len(insts)
+    C, K, Nt, Nr, d = pk.dims[0]
+    stream = torch.cuda.Stream(device=dev)
+    opts = pkg.default_opts(precision=args.precision)
+    if args.smem_budget:
+        opts.smem_budget = args.smem_budget
+    solver = pkg.Solver(batch, pk.dims[0], opts=opts, stream=stream)
+    H = torch.from_numpy(pk.H).to(dev)
+    G0 = torch.from_numpy(pk.G0).to(dev)
+    alpha = torch.from_numpy(pk.alpha).to(dev)
+    sigma2 = torch.from_numpy(pk.sigma2).to(dev)
+    P = torch.from_numpy(pk.P).to(dev)
+    wsr = torch.empty(batch, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    ev_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+
+    def one_step(pair=None):
+        solver.set_problem(H, alpha, sigma2, P)
+        solver.warmstart(G0)
+        if pair is not None:
+            pair[0].record(stream)
+        solver.step(ITERS)
+        if pair is not None:
+            pair[1].record(stream)
+        solver.wsr(wsr)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = solver.launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for s in range(args.steps):
+            one_step(ev_pairs[s])
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = solver.launches - l0
+    # duration of each launch of the iteration kernel, from events on its stream
+    iter_ms = [a.elapsed_time(b) for a, b in ev_pairs]
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * batch * args.steps / (elapsed_ms / 1000.0)
+
+    # ---- end to end through the C-ABI with host buffers (pinned)
+    Hh = torch.from_numpy(pk.H).pin_memory()
+    G0h = torch.from_numpy(pk.G0).pin_memory()
+    ah = torch.from_numpy(pk.alpha).pin_memory()
+    sh = torch.from_numpy(pk.sigma2).pin_memory()
+    Ph = torch.from_numpy(pk.P).pin_memory()
+    wsr_h = torch.empty(batch, dtype=torch.float64).pin_memory()
+    solver.solve_host(Hh, ah, sh, Ph, G0h, ITERS, wsr_h)  # warm-up (allocates its input buffers)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve_host(Hh, ah, sh, Ph, G0h, ITERS, wsr_h)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * batch * args.steps / e2e_s
+    h2d = pk.H.nbytes + pk.G0.nbytes + pk.alpha.nbytes + pk.sigma2.nbytes + pk.P.nbytes
+    d2h = batch * 8
+
+    # ---- parity sample: a few instances re-solved by the FP64 oracle
+    parity = None
+    st = torch.empty(batch, dtype=torch.int32, device=dev)
+    solver.status(st)
+    torch.cuda.synchronize()
+    n_bad_status = int((st != 0).sum().item())
+    got = wsr.cpu().numpy()
+    if rank == 0 and not args.no_parity:
+        from oracle import model as om
+        from oracle import solvers as osv
+        sample = [0, 2100, 4200, 7167]
+        gaps = []
+        for b in sample:
+            inst = insts[b]
+            inst.H = inst.H.astype(np.complex64).astype(np.complex128)
+            inst.G0 = inst.G0.astype(np.complex64).astype(np.complex128)
+            inst.alpha = inst.alpha.astype(np.float32).astype(np.float64)
+            V0 = osv.initial_precoder(inst.G0, inst.P)
+            r = osv.ammmse(inst.H, inst.sigma2, inst.alpha, inst.P, K, Nr, d, V0, ITERS)
+            want = om.wsr_bits(inst.H, r.V, inst.sigma2, inst.alpha, K, Nr, d)
+            gaps.append(abs(got[b] - want) / want)
+        parity = {"checked": len(sample), "max_wsr_gap": max(gaps), "bad_status": n_bad_status}
+
+    # ---- roofline of the dominant kernel (the fused iteration kernel)
+    peaks, src = measured_peaks()
+    flops_launch = algorithmic_gemm_flops(C, K, Nt, Nr, d) * ITERS * batch
+    avg_iter_ms = statistics.mean(iter_ms)
+    achieved = flops_launch / (avg_iter_ms / 1000.0) / 1e12
+    if args.precision == "fp32":
+        peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "iterate_kernel",
+                "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                             f"(derived; {src} clocks)"}
+    else:
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "iterate_kernel", "peak_note": f"bf16 burst, {src}"}
+
+    cpu = None
+    if pool is not None:
+        v, dt, n = oracle_throughput(pool, cores, 4 * cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} instances of the same workload (numpy float64 oracle, {ITERS} iterations each, "
+                         f"one process per core, {dt:.1f} s)"}
+        pool.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": batch, "iterations": ITERS,
+                   "precision": args.precision, "small_solves": "f64",
+                   "l2": "inputs larger than L2 (H: %.0f MB per GPU)" % (pk.H.nbytes / 1e6)},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "iterate_kernel_ms": avg_iter_ms,
+        "parity": parity,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--smem-budget", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -246,3 +246,48 @@ def random_small(rng: np.random.Generator, C: int, K: int, Nt: int, Nr: int, d: 
         P=(lambda g, n: P * g.uniform(0.5, 1.5, n)) if np.isscalar(P) else P,
         sigma2=lambda g, n: g.uniform(*sigma2_range, n),
         alpha=lambda g, n: g.uniform(*alpha_range, n))
+
+
+# --------------------------------------------------------------------------
+# Packing into the C-ABI layout (instances back to back; no arithmetic)
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Packed:
+    dims: List[tuple]          # (C, K, Nt, Nr, d) per instance
+    H: np.ndarray              # (h_elems,) complex
+    G0: np.ndarray             # (v_elems,) complex
+    alpha: np.ndarray          # (n_users,) float32
+    sigma2: np.ndarray         # (n_users,) float32
+    P: np.ndarray              # (n_cells,) float32
+    h_off: np.ndarray          # complex offsets per instance
+    v_off: np.ndarray
+
+    @property
+    def uniform(self) -> bool:
+        return all(d == self.dims[0] for d in self.dims)
+
+
+def pack(instances: Sequence[Instance], complex_dtype=np.complex64) -> Packed:
+    h_off, v_off = [], []
+    h = v = 0
+    for inst in instances:
+        h_off.append(h)
+        v_off.append(v)
+        h += inst.H.size
+        v += inst.G0.size
+    return Packed(
+        dims=[inst.dims for inst in instances],
+        H=np.concatenate([inst.H.reshape(-1) for inst in instances]).astype(complex_dtype),
+        G0=np.concatenate([inst.G0.reshape(-1) for inst in instances]).astype(complex_dtype),
+        alpha=np.concatenate([inst.alpha for inst in instances]).astype(np.float32),
+        sigma2=np.concatenate([inst.sigma2 for inst in instances]).astype(np.float32),
+        P=np.concatenate([inst.P for inst in instances]).astype(np.float32),
+        h_off=np.asarray(h_off, dtype=np.int64), v_off=np.asarray(v_off, dtype=np.int64))
+
+
+def unpack_V(packed: Packed, V: np.ndarray) -> List[np.ndarray]:
+    """Split a packed V buffer into per-instance (C, Nt, K*d) arrays."""
+    out = []
+    for (C, K, Nt, Nr, d), off in zip(packed.dims, packed.v_off):
+        out.append(V[off:off + C * Nt * K * d].reshape(C, Nt, K * d))
+    return out

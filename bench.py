@@ -44,6 +44,26 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
     return 2 * 8 * m * Nt * n * C
 
 
+def rank_base_seed(rank):
+    """Each rank solves its own disjoint set of instances (weak scaling)."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(value, dist, device=None):
+    """Max of a per-rank float over the process group (identity without one)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, per_rank_units, steps, seconds):
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * per_rank_units * steps / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -178,6 +198,28 @@ def run_reference(args):
     return 0
 
 
+def run_e2e(solver, pk, batch, args, dist, dev, world):
+    """The same metric through amm_solve_host: host (pinned) inputs copied in
+    and the WSR copied out inside the timed region."""
+    import torch
+    Hh = torch.from_numpy(pk.H).pin_memory()
+    G0h = torch.from_numpy(pk.G0).pin_memory()
+    ah = torch.from_numpy(pk.alpha).pin_memory()
+    sh = torch.from_numpy(pk.sigma2).pin_memory()
+    Ph = torch.from_numpy(pk.P).pin_memory()
+    wsr_h = torch.empty(batch, dtype=torch.float64).pin_memory()
+    solver.solve_host(Hh, ah, sh, Ph, G0h, ITERS, wsr_h)  # warm-up (allocates its input buffers)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve_host(Hh, ah, sh, Ph, G0h, ITERS, wsr_h)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    h2d = pk.H.nbytes + pk.G0.nbytes + pk.alpha.nbytes + pk.sigma2.nbytes + pk.P.nbytes
+    return whole_job_rate(world, batch, args.steps, e2e_s), h2d, batch * 8
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -205,7 +247,11 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
 
     # inputs of this rank (rank r uses a disjoint seed range)
-    insts = wl.single_cell_64(N_PER_P, base_seed=2 + 1000 * rank)
+    insts = wl.single_cell_64(N_PER_P, base_seed=rank_base_seed(rank))
+    if args.instances:
+        # an evenly spread subset of the batch (all seven P values), for profiling
+        step = max(1, len(insts) // args.instances)
+        insts = insts[::step][:args.instances]
     pk = wl.pack(insts)
     batch = len(insts)
     C, K, Nt, Nr, d = pk.dims[0]
@@ -260,34 +306,13 @@ def run_gpu(args):
     # duration of each launch of the iteration kernel, from events on its stream
     iter_ms = [a.elapsed_time(b) for a, b in ev_pairs]
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * batch * args.steps / (elapsed_ms / 1000.0)
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
+    value = whole_job_rate(world, batch, args.steps, elapsed_ms / 1000.0)
 
     # ---- end to end through the C-ABI with host buffers (pinned)
-    Hh = torch.from_numpy(pk.H).pin_memory()
-    G0h = torch.from_numpy(pk.G0).pin_memory()
-    ah = torch.from_numpy(pk.alpha).pin_memory()
-    sh = torch.from_numpy(pk.sigma2).pin_memory()
-    Ph = torch.from_numpy(pk.P).pin_memory()
-    wsr_h = torch.empty(batch, dtype=torch.float64).pin_memory()
-    solver.solve_host(Hh, ah, sh, Ph, G0h, ITERS, wsr_h)  # warm-up (allocates its input buffers)
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        solver.solve_host(Hh, ah, sh, Ph, G0h, ITERS, wsr_h)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * batch * args.steps / e2e_s
-    h2d = pk.H.nbytes + pk.G0.nbytes + pk.alpha.nbytes + pk.sigma2.nbytes + pk.P.nbytes
-    d2h = batch * 8
-
+    e2e_value, h2d, d2h = None, 0, 0
+    if not args.no_e2e:
+        e2e_value, h2d, d2h = run_e2e(solver, pk, batch, args, dist, dev, world)
     # ---- parity sample: a few instances re-solved by the FP64 oracle
     parity = None
     st = torch.empty(batch, dtype=torch.int32, device=dev)
@@ -298,7 +323,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_parity:
         from oracle import model as om
         from oracle import solvers as osv
-        sample = [0, 2100, 4200, 7167]
+        sample = sorted({0, batch // 3, (2 * batch) // 3, batch - 1})
         gaps = []
         for b in sample:
             inst = insts[b]
@@ -345,7 +370,8 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (H: %.0f MB per GPU)" % (pk.H.nbytes / 1e6)},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                if e2e_value is not None else None),
         "gpu_launches": launches,
         "clocks": clk,
         "iterate_kernel_ms": avg_iter_ms,
@@ -369,6 +395,9 @@ def main():
     ap.add_argument("--smem-budget", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="solve an evenly spread subset of the batch (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -18,6 +18,10 @@ __global__ void normalize_kernel(const InstDesc* desc, const float2* Hin, const 
                                  const float* P, float2* Hout, Scalars* sc);
 __global__ void init_kernel(const InstDesc* desc, const float2* V0, const float* P, float2* V, float2* Vprev,
                             Scalars* sc, float* gamma_c, int switch_iter);
+__global__ void tc_iterate_kernel(IterParams p, int prec);
+__global__ void wmmse_kernel(IterParams p, float bisect_tol, int bisect_max);
+int wmmse_plan_bytes(const InstDesc* desc, int batch, int budget);
+int tc_plan_bytes(const InstDesc* desc, int batch, int budget, int lanczos_steps, int prec);
 
 // Gather / scatter of the per-instance scalars for amm_get_state / amm_set_state.
 __global__ void get_scalars_kernel(const Scalars* sc, int n, int* t, int* stage, int* stage_iter, double* rho_prev,
@@ -73,6 +77,8 @@ struct amm_ctx {
   double* wsr_dev = nullptr;
   int smem_budget = 0;
   int smem_bytes = 0;
+  int tc_bytes = 0;  // shared memory of the tensor-core kernel (0: plain path)
+  int wm_bytes = 0;  // shared memory of the WMMSE kernel (-1: sizes it does not cover)
   bool problem_set = false;
   bool started = false;
   std::string err;
@@ -159,8 +165,6 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
   if (opts) o = *opts;
   if (o.precision != AMM_FP32 && o.precision != AMM_BF16 && o.precision != AMM_BF16X3)
     return fail(nullptr, AMM_EINVAL, "unknown precision");
-  if (o.precision != AMM_FP32)
-    return fail(nullptr, AMM_EUNSUPPORTED, "tensor-core precisions are not available for this configuration");
   if (o.u_at_extrapolated) return fail(nullptr, AMM_EUNSUPPORTED, "u_at_extrapolated = 1 is not implemented");
   if (o.step_rule < 0 || o.step_rule > 2 || o.tc < 0 || !(o.eps1 >= 0) || !(o.eps2 >= 0))
     return fail(nullptr, AMM_EINVAL, "bad step_rule / tc / eps");
@@ -220,6 +224,16 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
   }
   c->smem_budget = budget;
   c->smem_bytes = smem;
+  c->wm_bytes = amm::wmmse_plan_bytes(c->hdesc.data(), batch, budget);
+  if (o.precision != AMM_FP32) {
+    const int tcb = amm::tc_plan_bytes(c->hdesc.data(), batch, budget, o.lanczos_steps, o.precision);
+    if (tcb < 0) {
+      delete c;
+      return fail(nullptr, AMM_EUNSUPPORTED,
+                  "the tensor-core path needs one cell, 2*C*K*Nr <= 128, 2*Nt <= 128 and K*d <= 96");
+    }
+    c->tc_bytes = tcb;
+  }
 
   cudaError_t e = cudaSuccess;
   if ((e = dalloc(&c->ddesc, batch)) || (e = dalloc(&c->H, h)) || (e = dalloc(&c->alpha, u)) ||
@@ -233,7 +247,11 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
   }
   if ((e = cudaMemcpy(c->ddesc, c->hdesc.data(), sizeof(InstDesc) * batch, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(Scalars) * batch)) ||
-      (e = cudaFuncSetAttribute(amm::iterate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) {
+      (e = cudaFuncSetAttribute(amm::iterate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) ||
+      (c->tc_bytes > 0 && (e = cudaFuncSetAttribute(amm::tc_iterate_kernel,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, c->tc_bytes))) ||
+      (c->wm_bytes > 0 && (e = cudaFuncSetAttribute(amm::wmmse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    c->wm_bytes)))) {
     free_all(c);
     delete c;
     return fail(nullptr, AMM_ECUDA, std::string("set-up failed: ") + cudaGetErrorString(e));
@@ -306,6 +324,10 @@ static amm::IterParams base_params(amm_ctx* c) {
 }
 
 static amm_status launch_iterate(amm_ctx* c, const amm::IterParams& p) {
+  if (c->tc_bytes > 0 && p.mode != amm::kEvalWsr) {
+    amm::tc_iterate_kernel<<<c->batch, amm::kThreads, c->tc_bytes, c->stream>>>(p, c->opts.precision);
+    return check_launch(c, "tc_iterate_kernel");
+  }
   amm::iterate_kernel<<<c->batch, amm::kThreads, c->smem_bytes, c->stream>>>(p);
   return check_launch(c, "iterate_kernel");
 }
@@ -345,10 +367,17 @@ extern "C" amm_status amm_wsr(amm_ctx* c, double* wsr) {
 
 extern "C" amm_status amm_wmmse_step(amm_ctx* c, int n_iters, double bisect_tol, int bisect_max) {
   if (!c) return AMM_EINVAL;
-  (void)n_iters;
-  (void)bisect_tol;
-  (void)bisect_max;
-  return fail(c, AMM_EUNSUPPORTED, "amm_wmmse_step is not available in this build");
+  if (n_iters < 0 || !(bisect_tol > 0) || bisect_max < 1)
+    return fail(c, AMM_EINVAL, "amm_wmmse_step: need n_iters >= 0, bisect_tol > 0, bisect_max >= 1");
+  if (!c->started) return fail(c, AMM_EINVAL, "amm_wmmse_step before amm_warmstart");
+  if (c->wm_bytes < 0)
+    return fail(c, AMM_EUNSUPPORTED, "amm_wmmse_step: an Nt x Nt system of these sizes does not fit shared memory");
+  if (n_iters == 0) return AMM_OK;
+  amm::IterParams p = base_params(c);
+  p.n_iters = n_iters;
+  p.mode = amm::kFixed;
+  amm::wmmse_kernel<<<c->batch, amm::kThreads, c->wm_bytes, c->stream>>>(p, (float)bisect_tol, bisect_max);
+  return check_launch(c, "wmmse_kernel");
 }
 
 extern "C" amm_status amm_get_V(const amm_ctx* cc, void* V) {

@@ -1,0 +1,560 @@
+// Device routines shared by the solver kernels: block-wide complex GEMM,
+// TMA bulk staging, the FP64 per-user Hermitian solves and the Lanczos
+// estimate of ||F_k||_2.  Included by each kernel translation unit.
+#pragma once
+
+#include <math.h>
+
+#include "amm_internal.cuh"
+
+namespace amm {
+
+// ------------------------------------------------------------------ GEMM
+// Block-wide complex GEMM with a (TM x TN) register tile per thread; the
+// rows of a tile are r = tr + i*ntr and its columns c = tc + j*ntc, so a
+// warp reads consecutive columns of B.  OPA = 0: A(r,p) = A[r*lda + p];
+// OPA = 1: A(r,p) = conj(A[p*lda + r]).  epi(r, c, value) for r < M, c < N.
+template <int TM, int TN, int OPA, class Epi>
+__device__ __forceinline__ void block_cgemm(int M, int N, int KK, const float2* __restrict__ A, int lda,
+                                            const float2* __restrict__ B, int ldb, Epi epi) {
+  const int ntr = (M + TM - 1) / TM, ntc = (N + TN - 1) / TN;
+  const int ntiles = ntr * ntc;
+  for (int tile = threadIdx.x; tile < ntiles; tile += blockDim.x) {
+    const int tr = tile / ntc, tc = tile - tr * ntc;
+    const float2* Ap[TM];
+    const float2* Bp[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      int r = tr + i * ntr;
+      r = (r < M) ? r : 0;  // out-of-range rows read row 0; their results are dropped
+      Ap[i] = (OPA == 0) ? A + (long long)r * lda : A + r;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int c = tc + j * ntc;
+      c = (c < N) ? c : 0;
+      Bp[j] = B + c;
+    }
+    float2 acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int p = 0; p < KK; ++p) {
+      float2 a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = (OPA == 0) ? Ap[i][p] : Ap[i][(long long)p * lda];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bp[j][(long long)p * ldb];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+          acc[i][j] = (OPA == 0) ? cfma(a[i], bb[j], acc[i][j]) : cjfma(a[i], bb[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int r = tr + i * ntr;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int c = tc + j * ntc;
+        if (r < M && c < N) epi(r, c, acc[i][j]);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- bulk staging
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Copy `rows` rows of `cols` complex elements from global (row stride
+// gld) to shared memory (row stride sld).  Rows whose addresses and length
+// are 16-byte multiples go through the TMA bulk-copy engine
+// (cp.async.bulk) tracked by one mbarrier; anything else is copied by the
+// threads.  Every wait is bounded by spin_budget; on timeout the status
+// flag is set.  Contains __syncthreads().
+static __device__ __noinline__ void stage_rows(float2* dst, int sld, const float2* src, long long gld, int rows, int cols,
+                           uint64_t* mbar, unsigned& phase, long long spin_budget, int* fail) {
+  const bool bulk = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && ((gld & 1) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && ((sld & 1) == 0) && ((cols & 1) == 0) &&
+                    (cols > 0) && ((long long)rows * cols * 8 < (1 << 20));
+  if (!bulk) {
+    for (long long e = threadIdx.x; e < (long long)rows * cols; e += blockDim.x) {
+      const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+      dst[(long long)r * sld + c] = src[(long long)r * gld + c];
+    }
+    __syncthreads();
+    return;
+  }
+  const unsigned bytes = (unsigned)cols * 8u;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"(bytes * (unsigned)rows)
+                 : "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x < 32) {
+    for (int r = threadIdx.x; r < rows; r += 32) {
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(dst + (long long)r * sld)),
+          "l"(src + (long long)r * gld), "r"(bytes), "r"(smem_u32(mbar))
+          : "memory");
+    }
+  }
+  // bounded wait for the phase to complete: spin on test_wait for at most
+  // spin_budget SM clock cycles
+  unsigned done = 0;
+  const long long t0 = clock64();
+  while (true) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(phase)
+        : "memory");
+    if (done || clock64() - t0 > spin_budget) break;
+  }
+  if (!done) atomicExch(fail, kTimeout);
+  phase ^= 1u;
+  __syncthreads();
+}
+
+// ------------------------------------------------------- small FP64 solves
+// One thread per user.  Q: packed upper triangle (a <= b, row-major) of the
+// interference-plus-noise covariance; zo(a, s): own-stream block of Z.
+// Outputs U (NR x DD), UW = U W^{II} (NR x DD) and log det(I + M).
+template <int NR, int DD>
+__device__ bool small_solve(const float2* Qp, const float2* Zrow0, int ldz, int own0, float2* U, float2* UW,
+                            double* logdet, bool want_u) {
+  dcx L[NR][NR];
+  double inv[NR];
+  {
+    int q = 0;
+    dcx Q[NR][NR];
+#pragma unroll
+    for (int a = 0; a < NR; ++a)
+#pragma unroll
+      for (int b = a; b < NR; ++b) {
+        Q[a][b] = dc(Qp[q++]);
+        Q[b][a] = dconj(Q[a][b]);
+      }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      double dj = Q[j][j].x;
+#pragma unroll
+      for (int k = 0; k < j; ++k) dj -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
+      if (!(dj > 0.0)) return false;
+      const double rj = rsqrt(dj);
+      inv[j] = rj;
+      L[j][j] = dc(dj * rj, 0.0);
+#pragma unroll
+      for (int i = j + 1; i < NR; ++i) {
+        dcx s = Q[i][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = dfmsj(L[i][k], L[j][k], s);
+        L[i][j] = dscale(s, rj);
+      }
+    }
+  }
+  // X = L^{-1} Z_own
+  dcx X[NR][DD];
+#pragma unroll
+  for (int c = 0; c < DD; ++c)
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      dcx s = dc(Zrow0[(long long)i * ldz + own0 + c]);
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = dfms(L[i][k], X[k][c], s);
+      X[i][c] = dscale(s, inv[i]);
+    }
+  // I + M = I + X^H X (lower part) and its Cholesky factor R
+  dcx R[DD][DD];
+  double rinv[DD];
+  double pivprod = 1.0;
+  {
+    dcx A[DD][DD];
+#pragma unroll
+    for (int a = 0; a < DD; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        dcx s = dc(a == b ? 1.0 : 0.0, 0.0);
+#pragma unroll
+        for (int i = 0; i < NR; ++i) s = djfma(X[i][a], X[i][b], s);
+        A[a][b] = s;  // (X^H X)[a][b] = sum_i conj(X[i][a]) X[i][b]
+      }
+#pragma unroll
+    for (int j = 0; j < DD; ++j) {
+      double dj = A[j][j].x;
+#pragma unroll
+      for (int k = 0; k < j; ++k) dj -= R[j][k].x * R[j][k].x + R[j][k].y * R[j][k].y;
+      if (!(dj > 0.0)) return false;
+      pivprod *= dj;
+      const double rj = rsqrt(dj);
+      rinv[j] = rj;
+      R[j][j] = dc(dj * rj, 0.0);
+#pragma unroll
+      for (int i = j + 1; i < DD; ++i) {
+        dcx s = A[i][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = dfmsj(R[i][k], R[j][k], s);
+        R[i][j] = dscale(s, rj);
+      }
+    }
+  }
+  *logdet = log(pivprod);
+  if (!want_u) return true;
+  // UW = L^{-H} X = Q^{-1} Z_own
+  dcx Y[NR][DD];
+#pragma unroll
+  for (int c = 0; c < DD; ++c)
+#pragma unroll
+    for (int i = NR - 1; i >= 0; --i) {
+      dcx s = X[i][c];
+#pragma unroll
+      for (int k = i + 1; k < NR; ++k) s = dfms(dconj(L[k][i]), Y[k][c], s);
+      Y[i][c] = dscale(s, inv[i]);
+    }
+  // (I+M)^{-1} = R^{-H} R^{-1}: Rinv lower triangular
+  dcx Ri[DD][DD];
+#pragma unroll
+  for (int j = 0; j < DD; ++j) {
+    Ri[j][j] = dc(rinv[j], 0.0);
+#pragma unroll
+    for (int i = j + 1; i < DD; ++i) {
+      dcx s = dc(0.0, 0.0);
+#pragma unroll
+      for (int k = j; k < i; ++k) s = dfms(R[i][k], Ri[k][j], s);
+      Ri[i][j] = dscale(s, rinv[i]);
+    }
+  }
+  dcx Mi[DD][DD];
+#pragma unroll
+  for (int a = 0; a < DD; ++a)
+#pragma unroll
+    for (int b = 0; b < DD; ++b) {
+      dcx s = dc(0.0, 0.0);
+      const int k0 = a > b ? a : b;
+#pragma unroll
+      for (int k = 0; k < DD; ++k)
+        if (k >= k0) s = djfma(Ri[k][a], Ri[k][b], s);
+      Mi[a][b] = s;
+    }
+#pragma unroll
+  for (int i = 0; i < NR; ++i)
+#pragma unroll
+    for (int c = 0; c < DD; ++c) {
+      dcx s = dc(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < DD; ++b) s = dfma(Y[i][b], Mi[b][c], s);
+      U[i * DD + c] = tof(s);
+      UW[i * DD + c] = tof(Y[i][c]);
+    }
+  return true;
+}
+
+static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, const float2* Qp, const float2* Zrow0, int ldz, int own0,
+                                     float2* U, float2* UW, double* logdet, bool want_u) {
+#define AMM_SS(a, b) \
+  if (Nr == a && d == b) return small_solve<a, b>(Qp, Zrow0, ldz, own0, U, UW, logdet, want_u);
+  AMM_SS(1, 1)
+  AMM_SS(2, 1) AMM_SS(2, 2)
+  AMM_SS(3, 1) AMM_SS(3, 2) AMM_SS(3, 3)
+  AMM_SS(4, 1) AMM_SS(4, 2) AMM_SS(4, 3) AMM_SS(4, 4)
+#undef AMM_SS
+  return false;
+}
+
+// ------------------------------------------------------- Lanczos ||F_k||_2
+// Largest eigenvalue of the Lanczos tridiagonal T (diagonal a, off-diagonal
+// b) by multisection on the Sturm count, run by warp 0 (FP32).
+static __device__ __noinline__ float tridiag_max_eig(const float* a, const float* b, int n) {
+  const int lane = threadIdx.x & 31;
+  float lo = a[0], hi = a[0];
+  for (int i = 0; i < n; ++i) {
+    const float r = (i > 0 ? fabsf(b[i - 1]) : 0.f) + (i + 1 < n ? fabsf(b[i]) : 0.f);
+    lo = fmaxf(lo, a[i]);
+    hi = fmaxf(hi, a[i] + r);
+  }
+  const float scale = fmaxf(fabsf(hi), 1e-30f);
+  for (int round = 0; round < 8; ++round) {
+    const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+    // number of eigenvalues below x (negative pivots of T - x I)
+    int below = 0;
+    float q = a[0] - x;
+    if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
+    below += q < 0.f;
+    for (int i = 1; i < n; ++i) {
+      q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+      if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
+      below += q < 0.f;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, below < n);  // some eigenvalue >= x
+    if (mask == 0u) {
+      hi = lo + (hi - lo) / 33.f;
+    } else {
+      const int l = 31 - __clz(mask);
+      const float nlo = lo + (hi - lo) * (float)(l + 1) / 33.f;
+      const float nhi = (l == 31) ? hi : lo + (hi - lo) * (float)(l + 2) / 33.f;
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  return 0.5f * (lo + hi);
+}
+
+struct Views {
+  const float2* H;  // cell block j at H + j*m*ldh
+  int ldh;
+  float2* Z[2];
+  int ldz;
+  float2* V[2];     // cell block j at V + j*Nt*ldv
+  int ldv;
+  float2* QL;       // Krylov basis (Lm+1) x Nt
+};
+
+// Lanczos with full reorthogonalisation on F_k x = Htilde_k^H D Htilde_k x.
+// Returns lambda_max of the tridiagonal (a lower bound on ||F_k||_2 that is
+// exact when the Krylov space is invariant).  Contains __syncthreads().
+template <class HGet>
+__device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, const float2* sU, const float2* sP,
+                              const float* alpha_u, float2* QL, float2* y, float2* z, float2* w, float* ta, float* tb,
+                              float2* h, double* red, float* bcast) {
+  const int Nt = D.Nt, m = Ly.m, Nr = D.Nr, d = D.d;
+  const int tid = threadIdx.x;
+  // group of g threads per output row, g a power of two <= 32
+  int g = 1;
+  while (g < 32 && 2 * g * m <= (int)blockDim.x) g <<= 1;
+  int gN = 1;
+  while (gN < 32 && 2 * gN * Nt <= (int)blockDim.x) gN <<= 1;
+  // fixed start vector: unit-modulus entries with golden-ratio phases
+  const float rn = rsqrtf((float)Nt);
+  for (int p = tid; p < Nt; p += blockDim.x) {
+    float s, c;
+    sincosf(6.2831853f * 0.6180339887f * (float)(p + 1), &s, &c);
+    QL[p] = make_float2(c * rn, s * rn);
+  }
+  __syncthreads();
+  const int Lm = Ly.Lm;
+  int Leff = Lm;
+  float beta_prev = 0.f;
+  for (int j = 0; j < Lm; ++j) {
+    const float2* q = QL + (long long)j * Nt;
+    // y = Htilde_k q
+    for (int e0 = 0; e0 < m * g; e0 += blockDim.x) {  // warp-uniform trip count for the shuffles
+      const int e = e0 + tid;
+      const bool act = e < m * g;
+      const int i = act ? e / g : 0, l = e % g;
+      float2 acc = make_float2(0.f, 0.f);
+      if (act)
+        for (int p = l; p < Nt; p += g) acc = cfma(hget(i, p), q[p], acc);
+      for (int o = g >> 1; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, g);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, g);
+      }
+      if (act && l == 0) y[i] = acc;
+    }
+    __syncthreads();
+    // z_r = 2 alpha_r P_r (U_r^H y_r)
+    for (int i = tid; i < m; i += blockDim.x) {
+      const int r = i / Nr, a = i - r * Nr;
+      const float2* Ur = sU + r * Nr * d;
+      const float2* Pr = sP + r * Nr * d;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int s = 0; s < d; ++s) {
+        float2 ts = make_float2(0.f, 0.f);
+        for (int b = 0; b < Nr; ++b) ts = cjfma(Ur[b * d + s], y[r * Nr + b], ts);
+        acc = cfma(Pr[a * d + s], ts, acc);
+      }
+      z[i] = cscale(acc, 2.f * alpha_u[r]);
+    }
+    __syncthreads();
+    // w = Htilde_k^H z
+    for (int e0 = 0; e0 < Nt * gN; e0 += blockDim.x) {
+      const int e = e0 + tid;
+      const bool act = e < Nt * gN;
+      const int p = act ? e / gN : 0, l = e % gN;
+      float2 acc = make_float2(0.f, 0.f);
+      if (act)
+        for (int i = l; i < m; i += gN) acc = cjfma(hget(i, p), z[i], acc);
+      for (int o = gN >> 1; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, gN);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, gN);
+      }
+      if (act && l == 0) w[p] = acc;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int p = tid; p < Nt; p += blockDim.x) part += (double)(q[p].x * w[p].x + q[p].y * w[p].y);
+    const float aj = (float)block_sum(part, red);
+    const float2* qm = (j > 0) ? QL + (long long)(j - 1) * Nt : q;
+    for (int p = tid; p < Nt; p += blockDim.x) {
+      float2 v = w[p];
+      v = csub(v, cscale(q[p], aj));
+      if (j > 0) v = csub(v, cscale(qm[p], beta_prev));
+      w[p] = v;
+    }
+    __syncthreads();
+    // two passes of classical Gram-Schmidt against q_0..q_j
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = tid >> 5; i <= j; i += blockDim.x >> 5) {
+        const float2* qi = QL + (long long)i * Nt;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int p = tid & 31; p < Nt; p += 32) acc = cjfma(qi[p], w[p], acc);
+        acc = warp_sum(acc);
+        if ((tid & 31) == 0) h[i] = acc;
+      }
+      __syncthreads();
+      for (int p = tid; p < Nt; p += blockDim.x) {
+        float2 v = w[p];
+        for (int i = 0; i <= j; ++i) v = csub(v, cmul(h[i], QL[(long long)i * Nt + p]));
+        w[p] = v;
+      }
+      __syncthreads();
+    }
+    double nn = 0.0;
+    for (int p = tid; p < Nt; p += blockDim.x) nn += (double)cabs2(w[p]);
+    const float bj = (float)sqrt(block_sum(nn, red));
+    if (tid == 0) {
+      ta[j] = aj;
+      tb[j] = bj;
+    }
+    if (j + 1 >= Lm || !(bj > 1e-6f * fabsf(aj))) {
+      Leff = j + 1;
+      break;
+    }
+    const float ib = 1.f / bj;
+    float2* qn = QL + (long long)(j + 1) * Nt;
+    for (int p = tid; p < Nt; p += blockDim.x) qn[p] = cscale(w[p], ib);
+    beta_prev = bj;
+    __syncthreads();
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const float lam = tridiag_max_eig(ta, tb, Leff);
+    if (tid == 0) *bcast = lam;
+  }
+  __syncthreads();
+  return *bcast;
+}
+
+
+// ------------------------------------------------------- per-user phases
+// S3a: upper triangle of Q_r = sigma^2 I + sum over streams other than the
+// user's own of z z^H (sigma^2 = 1 after normalisation).  zget(row, col).
+template <class ZGet>
+__device__ __forceinline__ void covariance_phase(const InstDesc& D, const Layout& Ly, ZGet zget, float2* sQ) {
+  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn, np = Ly.np;
+  for (int e = threadIdx.x; e < Ly.CK * np; e += blockDim.x) {
+    const int r = e / np;
+    int q = e - r * np, a = 0;
+    while (q >= Nr - a) {
+      q -= Nr - a;
+      ++a;
+    }
+    const int bb = a + q;
+    const int own0 = (r / K) * n + (r % K) * d;
+    float2 acc = make_float2(a == bb ? 1.f : 0.f, 0.f);
+    for (int c = 0; c < Cn; ++c) {
+      if (c >= own0 && c < own0 + d) continue;
+      acc = cjfma(zget(r * Nr + bb, c), zget(r * Nr + a, c), acc);  // z_a conj(z_b)
+    }
+    sQ[e] = acc;
+  }
+}
+
+// S3b/S4: FP64 solves, one thread per user, then rho = sum alpha_r R_r
+// (block-uniform).  own-stream block of user r: rows r*Nr.., columns own0..
+// of the Z view (zrow0(r) gives row r*Nr, ldz its row stride).
+__device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& Ly, const float2* Z, int ldz,
+                                              const float2* sQ, float2* sU, float2* sUW, double* sRho,
+                                              const float* alpha_u, bool want_u, double* red, int* fail) {
+  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, np = Ly.np, CK = Ly.CK;
+  for (int r = threadIdx.x; r < CK; r += blockDim.x) {
+    const int own0 = (r / K) * n + (r % K) * d;
+    double ld = 0.0;
+    const bool ok = small_solve_dispatch(Nr, d, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
+                                         sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u);
+    if (!ok || !isfinite(ld)) atomicExch(fail, kNumeric);
+    sRho[r] = ok ? ld : 0.0;
+  }
+  __syncthreads();
+  double part = 0.0;
+  for (int r = threadIdx.x; r < CK; r += blockDim.x) part += (double)alpha_u[r] * sRho[r];
+  return block_sum(part, red);
+}
+
+// S6: Y_r = 2 alpha_r P_r (U_r^H zhat_r - S_r) for every user r and stream
+// column c; sink(row, c, value) receives Y[row][c] for the Nr rows of r.
+template <class ZGet, class Sink>
+__device__ __forceinline__ void gradient_rhs_phase(const InstDesc& D, const Layout& Ly, ZGet zhat,
+                                                   const float2* sU, const float2* sP, const float* alpha_u,
+                                                   Sink sink) {
+  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn;
+  for (int e = threadIdx.x; e < Ly.CK * Cn; e += blockDim.x) {
+    const int r = e / Cn, c = e - r * Cn;
+    const int own0 = (r / K) * n + (r % K) * d;
+    const float2* Ur = sU + r * Nr * d;
+    const float2* Pr = sP + r * Nr * d;
+    float2 zh[kMaxNr];
+#pragma unroll
+    for (int a = 0; a < kMaxNr; ++a)
+      if (a < Nr) zh[a] = zhat(r * Nr + a, c);
+    float2 ts[kMaxNr];
+#pragma unroll
+    for (int s = 0; s < kMaxNr; ++s) {
+      if (s < d) {
+        float2 acc = make_float2((c - own0 == s) ? -1.f : 0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < kMaxNr; ++a)
+          if (a < Nr) acc = cjfma(Ur[a * d + s], zh[a], acc);
+        ts[s] = acc;
+      }
+    }
+    const float sc2 = 2.f * alpha_u[r];
+#pragma unroll
+    for (int a = 0; a < kMaxNr; ++a) {
+      if (a < Nr) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < kMaxNr; ++s)
+          if (s < d) acc = cfma(Pr[a * d + s], ts[s], acc);
+        sink(r * Nr + a, c, cscale(acc, sc2));
+      }
+    }
+  }
+}
+
+// Stage test of Algorithm 3 and the stopping test, run by one thread.
+// ctrl: [0] t, [1] stage, [2] stage_iter, [3] last_stage, [4] stop,
+// [6] step flags (bit 0 spectral, bit 1 freeze gamma_c).
+__device__ __forceinline__ void stage_logic(int* ctrl, double rho, double rho_prev, int mode, float eps1,
+                                            float eps2, int switch_iter, int step_rule, int tc) {
+  const int t = ctrl[0];
+  const bool have_prev = !isnan(rho_prev);
+  const double rel = have_prev ? fabs(rho - rho_prev) / fabs(rho_prev) : INFINITY;
+  int stop = 0;
+  if (mode == kTolerance && ctrl[3] == 2 && rel <= (double)eps2) stop = 1;
+  int stage = ctrl[1], si = ctrl[2];
+  if (!stop) {
+    if (stage == 1) {
+      const bool go = (switch_iter >= 1) ? (t >= switch_iter) : (rel <= (double)eps1);
+      if (go) {
+        stage = 2;
+        si = 0;
+      }
+    }
+    si += 1;
+    ctrl[1] = stage;
+    ctrl[2] = si;
+    const int spectral = (step_rule == 1) || (step_rule == 0 && si <= tc);
+    ctrl[6] = spectral | ((step_rule == 0 && si == tc) ? 2 : 0);
+  }
+  ctrl[4] = stop;
+}
+
+}  // namespace amm

@@ -1,0 +1,442 @@
+// Fused A-MMMSE iteration kernel on the fifth-generation tensor cores
+// (tcgen05, sm_103a): same algorithm and per-user FP64 solves as the plain
+// kernel, but the two complex GEMMs of each iteration run as real BF16
+// products with FP32 accumulation in tensor memory.
+//
+// Real embedding (one M = 128 tile per GEMM; single cell, 2m <= 128, 2Nt <= 128):
+//   forward   [Zr; Zi] = [[Hr, -Hi], [Hi, Hr]] [Vr; Vi]            (A1 = H_real, B1 = V_real^T)
+//   gradient  [Gr; Gi] = [[Hr^T, Hi^T], [-Hi^T, Hr^T]] [Yr; Yi]    (A2 = H_real^T, B2 = Y_real^T)
+// so G = H^H Y exactly as the gradient of eq. (14).  BF16X3 splits every
+// operand x = hi + lo and accumulates hi*hi + hi*lo + lo*hi.
+//
+// Tensor memory holds the FP32 state between iterations: Z(V^{t-1}) and
+// Z(V^{t-2}) (two forward accumulators used alternately, so the
+// extrapolated receiver input Z(Vhat) = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) needs
+// no extra GEMM), the gradient accumulator, and V^{t-1}, V^{t-2} in the same
+// row layout as the gradient (lane p = row p of [Vr; Vi]), so the
+// extrapolation, step and projection of eqs. (13), (15), (17) are lane-local.
+#include <math.h>
+
+#include "amm_device.cuh"
+#include "amm_tc.cuh"
+
+namespace amm {
+
+struct TcLayout {
+  Layout base;  // the small per-user region (offsets from the plain plan)
+  int K1p, K2p, Np, Bk, ncols;
+  int off_A1h, off_A1l, off_A2h, off_A2l, off_Bh, off_Bl, off_Zs, off_L;
+  int total;
+  bool ok;
+};
+
+__host__ __device__ inline TcLayout plan_tc(const InstDesc& D, int budget, int lanczos_steps, int prec) {
+  TcLayout T;
+  T.base = plan_layout(D, 0, lanczos_steps);  // budget 0: only the small region
+  const int m = T.base.m, n = T.base.n;
+  T.K1p = align_up(2 * D.Nt, 16);
+  T.K2p = align_up(2 * m, 16);
+  T.Np = align_up(n < 16 ? 16 : n, 16);
+  T.Bk = T.K1p > T.K2p ? T.K1p : T.K2p;
+  int need = 5 * T.Np;
+  T.ncols = 32;
+  while (T.ncols < need) T.ncols <<= 1;
+  const bool x3 = (prec == 2);
+  int off = align_up(T.base.total, 1024);
+  T.off_A1h = off; off += 128 * T.K1p * 2;
+  T.off_A1l = off; off += x3 ? 128 * T.K1p * 2 : 0;
+  T.off_A2h = off; off += 128 * T.K2p * 2;
+  T.off_A2l = off; off += x3 ? 128 * T.K2p * 2 : 0;
+  T.off_Bh = off;  off += T.Np * T.Bk * 2;
+  T.off_Bl = off;  off += x3 ? T.Np * T.Bk * 2 : 0;
+  T.off_Zs = off;  off += m * T.base.ldz * 8;
+  off = align_up(off, 16);
+  const int szL = (T.base.Lm + 1) * D.Nt * 8;
+  T.off_L = -1;
+  if (off + szL <= budget) { T.off_L = off; off += szL; }
+  T.total = off;
+  T.ok = D.C == 1 && 2 * m <= 128 && 2 * D.Nt <= 128 && T.ncols <= 512 && off <= budget;
+  return T;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, int prec) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar;
+  __shared__ unsigned s_tmem;
+  __shared__ int s_fail;
+  __shared__ int s_ctrl[8];
+  __shared__ float s_bcast;
+  __shared__ float s_scale;
+
+  const int b = blockIdx.x;
+  const InstDesc D = p.desc[b];
+  Scalars* scg = p.sc + b;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Nt = D.Nt;
+  const TcLayout T = plan_tc(D, p.smem_budget, p.lanczos_steps, prec);
+  const Layout& Ly = T.base;
+  const int m = Ly.m, n = Ly.n, ldz = Ly.ldz;
+  const bool x3 = (prec == 2);
+
+  if (tid == 0) {
+    const int st = scg->status;
+    s_fail = (st == kNumeric || st == kTimeout) ? st : kOk;
+    s_ctrl[0] = scg->t;
+    s_ctrl[1] = scg->stage;
+    s_ctrl[2] = scg->stage_iter;
+    s_ctrl[3] = scg->last_stage;
+    s_ctrl[4] = 0;
+    s_ctrl[5] = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (s_fail != kOk) return;  // before any tensor-memory allocation
+  if (warp == 0) tc::tmem_alloc(&s_tmem, (unsigned)T.ncols);
+
+  double* red = reinterpret_cast<double*>(smem + Ly.off_red);
+  float* cellf = reinterpret_cast<float*>(smem + Ly.off_cell);
+  float2* sU = reinterpret_cast<float2*>(smem + Ly.off_U);
+  float2* sUW = reinterpret_cast<float2*>(smem + Ly.off_UW);
+  float2* sQ = reinterpret_cast<float2*>(smem + Ly.off_Q);
+  double* sRho = reinterpret_cast<double*>(smem + Ly.off_rho);
+  float2* ly = reinterpret_cast<float2*>(smem + Ly.off_y);
+  float2* lz = reinterpret_cast<float2*>(smem + Ly.off_z);
+  float2* lw = reinterpret_cast<float2*>(smem + Ly.off_w);
+  float* ta = reinterpret_cast<float*>(smem + Ly.off_tri);
+  float* tb = ta + (Ly.Lm + 1);
+  float2* lh = reinterpret_cast<float2*>(smem + Ly.off_h);
+  unsigned char* A1h = smem + T.off_A1h;
+  unsigned char* A1l = smem + T.off_A1l;
+  unsigned char* A2h = smem + T.off_A2h;
+  unsigned char* A2l = smem + T.off_A2l;
+  unsigned char* Bh = smem + T.off_Bh;
+  unsigned char* Bl = smem + T.off_Bl;
+  float2* Zs = reinterpret_cast<float2*>(smem + T.off_Zs);
+  float2* QL = (T.off_L >= 0) ? reinterpret_cast<float2*>(smem + T.off_L) : p.Lws + D.l_off;
+
+  const float* alpha_u = p.alpha + D.u_off;
+  const float Pc = p.P[D.c_off];
+  float* gamma_c = p.gamma_c + D.c_off;
+  float2* Vg = p.V + D.v_off;
+  float2* Vpg = p.Vprev + D.v_off;
+  const float2* Hg = p.H + D.h_off;
+
+  // ---- zero the operand buffers (padding rows / K columns must read as 0)
+  {
+    uint4* z4 = reinterpret_cast<uint4*>(smem + T.off_A1h);
+    const int n4 = (T.off_Zs - T.off_A1h) / 16;
+    for (int e = tid; e < n4; e += blockDim.x) z4[e] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const unsigned tbase = s_tmem;
+  const int Np = T.Np;
+  const unsigned colD1[2] = {0u, (unsigned)Np};
+  const unsigned colD2 = 2u * Np;
+  const unsigned colV[2] = {3u * Np, 4u * Np};
+
+  // ---- A operands from the normalised channel
+  for (int e = tid; e < m * Nt; e += blockDim.x) {
+    const int i = e / Nt, q = e - i * Nt;
+    const float2 h = Hg[e];
+    __nv_bfloat16 rh, rl, ih, il;
+    tc::split_bf16(h.x, rh, rl);
+    tc::split_bf16(h.y, ih, il);
+    const __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
+    auto put = [&](unsigned char* Ah, unsigned char* Al, int row, int k, int Kp, __nv_bfloat16 vh,
+                   __nv_bfloat16 vl) {
+      *reinterpret_cast<__nv_bfloat16*>(Ah + tc::kmaj_off(row, k, Kp)) = vh;
+      if (x3) *reinterpret_cast<__nv_bfloat16*>(Al + tc::kmaj_off(row, k, Kp)) = vl;
+    };
+    put(A1h, A1l, i, q, T.K1p, rh, rl);            // Hr
+    put(A1h, A1l, i, Nt + q, T.K1p, nih, nil);     // -Hi
+    put(A1h, A1l, m + i, q, T.K1p, ih, il);        // Hi
+    put(A1h, A1l, m + i, Nt + q, T.K1p, rh, rl);   // Hr
+    put(A2h, A2l, q, i, T.K2p, rh, rl);            // Hr^T
+    put(A2h, A2l, q, m + i, T.K2p, ih, il);        // Hi^T
+    put(A2h, A2l, Nt + q, i, T.K2p, nih, nil);     // -Hi^T
+    put(A2h, A2l, Nt + q, m + i, T.K2p, rh, rl);   // Hr^T
+  }
+
+  // lane-owner mapping of the tensor-memory rows: warp w reads lanes of
+  // quarter w%4 and the 16-column chunks h, h+2, ... (h = w/4)
+  const int quarter = warp & 3, half = warp >> 2;
+  const int R = quarter * 32 + lane;
+  const unsigned lane_addr = tbase + ((unsigned)(quarter * 32) << 16);
+  const int nchunks = Np / 16;
+
+  // V state rows: R < Nt real part of row R, Nt <= R < 2Nt imaginary part
+  auto load_state = [&](const float2* src, unsigned col) {
+    for (int cc = half; cc < nchunks; cc += 2) {
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = cc * 16 + j;
+        float x = 0.f;
+        if (c < n && R < Nt) x = src[(long long)R * n + c].x;
+        else if (c < n && R < 2 * Nt) x = src[(long long)(R - Nt) * n + c].y;
+        v[j] = x;
+      }
+      tc::tmem_st16(lane_addr + col + cc * 16, v);
+    }
+    tc::tmem_wait_st();
+  };
+  // B1 = V_real^T (K-major, K index = R) from a V state slot
+  auto write_B1 = [&](unsigned col) {
+    for (int cc = half; cc < nchunks; cc += 2) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + col + cc * 16, v);
+      if (R < T.K1p) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = cc * 16 + j;
+          if (c < n) {
+            __nv_bfloat16 hi, lo;
+            tc::split_bf16(v[j], hi, lo);
+            *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, R, T.K1p)) = hi;
+            if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, R, T.K1p)) = lo;
+          }
+        }
+      }
+    }
+  };
+  unsigned phase = 0;
+  auto gemm = [&](unsigned dcol, unsigned char* Ahi, unsigned char* Alo, int Kp) -> bool {
+    // operands written by the threads -> visible to the tensor core
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t idesc = tc::idesc_bf16(128, Np);
+      const unsigned sbo = (unsigned)(Kp / 8) * 128u;
+      const unsigned ah = tc::su32(Ahi), al = tc::su32(Alo), bh = tc::su32(Bh), bl = tc::su32(Bl);
+      for (int kk = 0; kk < Kp / 16; ++kk) {
+        const unsigned off = (unsigned)kk * 256u;
+        tc::mma_bf16(tbase + dcol, tc::smem_desc(ah + off, 128u, sbo), tc::smem_desc(bh + off, 128u, sbo), idesc,
+                     kk > 0);
+        if (x3) {
+          tc::mma_bf16(tbase + dcol, tc::smem_desc(ah + off, 128u, sbo), tc::smem_desc(bl + off, 128u, sbo), idesc,
+                       1u);
+          tc::mma_bf16(tbase + dcol, tc::smem_desc(al + off, 128u, sbo), tc::smem_desc(bh + off, 128u, sbo), idesc,
+                       1u);
+        }
+      }
+      tc::commit(&mbar);
+    }
+    const bool ok = tc::mbar_wait(&mbar, phase, p.spin_budget);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok) {
+      atomicExch(&s_fail, kTimeout);
+      tc::mbar_wait(&mbar, phase ^ 1u, p.spin_budget);  // let the MMAs drain before the block moves on
+    }
+    __syncthreads();
+    return s_fail == kOk;
+  };
+
+  int cur = 0, zc = 0;
+  load_state(Vg, colV[0]);
+  load_state(Vpg, colV[1]);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (p.extrapolate && s_ctrl[0] >= 3) {
+    write_B1(colV[1]);
+    gemm(colD1[1], A1h, A1l, T.K1p);  // Z(V^{t-2})
+  }
+  write_B1(colV[0]);
+
+  double rho = 0.0;
+  for (int it = 0; it < p.n_iters && s_fail == kOk; ++it) {
+    const int t = s_ctrl[0];
+    const float omega = (p.extrapolate && t >= 3) ? (float)(t - 2) / (float)(t + 1) : 0.f;
+    // ---- S2: Z = H V^{t-1} on the tensor cores
+    if (!gemm(colD1[zc], A1h, A1l, T.K1p)) break;
+    // accumulator -> FP32 Z in shared memory (lane R < m: Re row R; m <= R < 2m: Im row R - m)
+    for (int cc = half; cc < nchunks; cc += 2) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + colD1[zc] + cc * 16, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = cc * 16 + j;
+        if (c < n && R < m) Zs[(long long)R * ldz + c].x = v[j];
+        else if (c < n && R < 2 * m) Zs[(long long)(R - m) * ldz + c].y = v[j];
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    // ---- S3/S4: covariance, FP64 solves, rho = WSR(V^{t-1}), stage test
+    covariance_phase(D, Ly, [&](int row, int c) { return Zs[(long long)row * ldz + c]; }, sQ);
+    __syncthreads();
+    rho = solve_phase(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true, red, &s_fail);
+    if (s_fail != kOk) break;
+    if (tid == 0)
+      stage_logic(s_ctrl, rho, scg->rho_prev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
+    __syncthreads();
+    if (s_ctrl[4]) break;
+    const int stage = s_ctrl[1];
+    const float2* sP = (stage == 2) ? sUW : sU;
+    // ---- S1: Z(Vhat) = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) into Zs
+    if (omega != 0.f) {
+      tc::fence_after_sync();
+      for (int cc = half; cc < nchunks; cc += 2) {
+        float v[16], vp[16];
+        tc::tmem_ld16(lane_addr + colD1[zc] + cc * 16, v);
+        tc::tmem_ld16(lane_addr + colD1[zc ^ 1] + cc * 16, vp);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = cc * 16 + j;
+          const float zh = (1.f + omega) * v[j] - omega * vp[j];
+          if (c < n && R < m) Zs[(long long)R * ldz + c].x = zh;
+          else if (c < n && R < 2 * m) Zs[(long long)(R - m) * ldz + c].y = zh;
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+    // ---- S6: B2 = Y_real^T (K-major, K index: Re rows then Im rows)
+    gradient_rhs_phase(
+        D, Ly, [&](int row, int c) { return Zs[(long long)row * ldz + c]; }, sU, sP, alpha_u,
+        [&](int row, int c, float2 y) {
+          __nv_bfloat16 hi, lo;
+          tc::split_bf16(y.x, hi, lo);
+          *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, row, T.K2p)) = hi;
+          if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, row, T.K2p)) = lo;
+          tc::split_bf16(y.y, hi, lo);
+          *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, m + row, T.K2p)) = hi;
+          if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, m + row, T.K2p)) = lo;
+        });
+    for (int e = tid; e < n * (T.K2p - 2 * m); e += blockDim.x) {  // K padding of B2
+      const int c = e / (T.K2p - 2 * m), k = 2 * m + e % (T.K2p - 2 * m);
+      *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, k, T.K2p)) = __float2bfloat16_rn(0.f);
+      if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, k, T.K2p)) = __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    // ---- S5: step size, eq. (16); Lanczos reads H back from the split operand
+    {
+      const int sflag = s_ctrl[6];
+      float gk;
+      if (sflag & 1) {
+        const float lam = lanczos_norm(
+            D, Ly,
+            [&](int i, int q) {
+              float re = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1h + tc::kmaj_off(i, q, T.K1p)));
+              float im =
+                  __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1h + tc::kmaj_off(m + i, q, T.K1p)));
+              if (x3) {
+                re += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1l + tc::kmaj_off(i, q, T.K1p)));
+                im += __bfloat162float(
+                    *reinterpret_cast<const __nv_bfloat16*>(A1l + tc::kmaj_off(m + i, q, T.K1p)));
+              }
+              return make_float2(re, im);
+            },
+            sU, sP, alpha_u, QL, ly, lz, lw, ta, tb, lh, red, &s_bcast);
+        gk = (lam > 0.f) ? 1.f / lam : 0.f;
+        if ((sflag & 2) && tid == 0) gamma_c[0] = gk;
+      } else {
+        gk = (p.gamma_user > 0.f) ? p.gamma_user : gamma_c[0];
+      }
+      if (tid == 0) cellf[0] = gk;
+    }
+    // ---- S6/S7: G = H^H Y on the tensor cores
+    if (!gemm(colD2, A2h, A2l, T.K2p)) break;
+    const float gj = cellf[0];
+    float nrm = 0.f;
+    for (int cc = half; cc < nchunks; cc += 2) {
+      float g[16], v[16], vp[16];
+      tc::tmem_ld16(lane_addr + colD2 + cc * 16, g);
+      tc::tmem_ld16(lane_addr + colV[cur] + cc * 16, v);
+      tc::tmem_ld16(lane_addr + colV[cur ^ 1] + cc * 16, vp);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = cc * 16 + j;
+        const float vh = (omega != 0.f) ? (1.f + omega) * v[j] - omega * vp[j] : v[j];
+        float vt = vh - gj * g[j];
+        if (!(c < n && R < 2 * Nt)) vt = 0.f;
+        nrm = fmaf(vt, vt, nrm);
+        v[j] = vt;
+      }
+      tc::tmem_st16(lane_addr + colV[cur ^ 1] + cc * 16, v);
+    }
+    tc::tmem_wait_st();
+    const double s = block_sum((double)nrm, red);
+    const float scale = (s > (double)Pc) ? (float)sqrt((double)Pc / s) : 1.f;
+    for (int cc = half; cc < nchunks; cc += 2) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + colV[cur ^ 1] + cc * 16, v);
+      if (scale != 1.f) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] *= scale;
+        tc::tmem_st16(lane_addr + colV[cur ^ 1] + cc * 16, v);
+      }
+    }
+    tc::tmem_wait_st();
+    cur ^= 1;
+    zc ^= 1;
+    write_B1(colV[cur]);
+    if (tid == 0) {
+      scg->rho_prev = rho;
+      s_ctrl[3] = stage;
+      s_ctrl[0] = t + 1;
+      s_ctrl[5] += 1;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  // ---- write the iterate back (lane R holds row R of [Vr; Vi])
+  if (s_fail == kOk || s_fail == kNotConv) {
+    for (int cc = half; cc < nchunks; cc += 2) {
+      float v[16], vp[16];
+      tc::tmem_ld16(lane_addr + colV[cur] + cc * 16, v);
+      tc::tmem_ld16(lane_addr + colV[cur ^ 1] + cc * 16, vp);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = cc * 16 + j;
+        if (c < n && R < Nt) {
+          Vg[(long long)R * n + c].x = v[j];
+          Vpg[(long long)R * n + c].x = vp[j];
+        } else if (c < n && R < 2 * Nt) {
+          Vg[(long long)(R - Nt) * n + c].y = v[j];
+          Vpg[(long long)(R - Nt) * n + c].y = vp[j];
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, (unsigned)T.ncols);
+  if (tid == 0) {
+    scg->t = s_ctrl[0];
+    scg->stage = s_ctrl[1];
+    scg->stage_iter = s_ctrl[2];
+    scg->last_stage = s_ctrl[3];
+    int st = s_fail;
+    if (p.mode == kTolerance) {
+      scg->iters_run = s_ctrl[5];
+      scg->done = s_ctrl[4];
+      if (p.iters_out) p.iters_out[b] = s_ctrl[5];
+      if (st == kOk && !s_ctrl[4]) st = kNotConv;
+    }
+    scg->status = st;
+  }
+}
+
+// Host-side query: can every instance of the batch use the tensor-core
+// kernel, and with how much shared memory?
+int tc_plan_bytes(const InstDesc* desc, int batch, int budget, int lanczos_steps, int prec) {
+  int mx = 0;
+  for (int b = 0; b < batch; ++b) {
+    const TcLayout T = plan_tc(desc[b], budget, lanczos_steps, prec);
+    if (!T.ok) return -1;
+    if (T.total > mx) mx = T.total;
+  }
+  return mx;
+}
+
+}  // namespace amm

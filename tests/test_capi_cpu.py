@@ -74,6 +74,10 @@ def test_create_rejects_bad_batch_and_options(lib):
     assert _create(lib, 1, [(1, 4, 8, 2, 2)], lanczos_steps=0)[0] == pkg.AMM_EINVAL
     assert _create(lib, 1, [(1, 4, 8, 2, 2)], precision=9)[0] == pkg.AMM_EINVAL
     assert _create(lib, 1, [(1, 4, 8, 2, 2)], u_at_extrapolated=1)[0] == pkg.AMM_EUNSUPPORTED
+    # the tensor-core path covers one cell with 2m <= 128, 2Nt <= 128
+    assert _create(lib, 1, [(2, 4, 8, 2, 2)], precision="bf16x3")[0] == pkg.AMM_EUNSUPPORTED
+    assert _create(lib, 1, [(1, 4, 80, 2, 2)], precision="bf16")[0] == pkg.AMM_EUNSUPPORTED
+    assert _create(lib, 1, [(1, 40, 16, 2, 2)], precision="bf16x3")[0] == pkg.AMM_EUNSUPPORTED
     st = lib.amm_create(None, 1, None, 1, None, None)
     assert st == pkg.AMM_EINVAL
 

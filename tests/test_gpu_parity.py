@@ -279,3 +279,24 @@ def test_solve_host_matches_device_path():
                    torch.from_numpy(pk.P), torch.from_numpy(pk.G0), 20, wsr, V)
     assert np.array_equal(wsr.numpy(), dev_wsr)
     g.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 4, 8, 2, 2), (2, 2, 6, 2, 1), (1, 6, 24, 4, 2)])
+def test_wmmse_step_matches_oracle(shape):
+    """amm_wmmse_step (Algorithm 2: eq. (9), eq. (10), eq. (12) with
+    bisection to width 1e-4, at most 100 halvings) against the oracle's
+    WMMSE from the same projected V^0."""
+    iters = 12
+    insts = small_batch(shape, 6, 7000 + sum(shape))
+    g = GpuRun(insts)
+    g.warmstart()
+    g.s.wmmse_step(iters, 1e-4, 100)
+    got = g.wsr()
+    assert np.all(g.status() == 0)
+    for b, inst in enumerate(insts):
+        V0 = osv.initial_precoder(inst.G0, inst.P)
+        _, hist, _ = osv.wmmse(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0, iters,
+                               tol=1e-4, max_bisect=100)
+        want = hist[-1] / np.log(2.0)
+        assert abs(got[b] - want) <= WSR_TOL * want, (shape, b, got[b], want)
+    g.close()

@@ -256,7 +256,7 @@ def run_gpu(args):
     batch = len(insts)
     C, K, Nt, Nr, d = pk.dims[0]
     stream = torch.cuda.Stream(device=dev)
-    opts = pkg.default_opts(precision=args.precision)
+    opts = pkg.default_opts(precision=args.precision, fp64_solves=0 if args.fp32_solves else 1)
     if args.smem_budget:
         opts.smem_budget = args.smem_budget
     solver = pkg.Solver(batch, pk.dims[0], opts=opts, stream=stream)
@@ -366,7 +366,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances_per_gpu": batch, "iterations": ITERS,
-                   "precision": args.precision, "small_solves": "f64",
+                   "precision": args.precision, "small_solves": "f32" if args.fp32_solves else "f64",
                    "l2": "inputs larger than L2 (H: %.0f MB per GPU)" % (pk.H.nbytes / 1e6)},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -396,6 +396,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp32-solves", action="store_true",
+                    help="run the per-user Hermitian solves in FP32 instead of FP64")
     ap.add_argument("--instances", type=int, default=0,
                     help="solve an evenly spread subset of the batch (profiling runs)")
     args = ap.parse_args()

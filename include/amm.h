@@ -59,7 +59,7 @@ typedef enum {
 } amm_status;
 
 /* Arithmetic of the two complex GEMMs of each iteration (Z = H V and the
- * gradient H^H Y).  The small Hermitian solves always run in FP64. */
+ * gradient H^H Y).  The small Hermitian solves are chosen by fp64_solves. */
 typedef enum {
   AMM_FP32 = 0,    /* CUDA-core FP32 FFMA GEMMs (the plain path) */
   AMM_BF16 = 1,    /* tcgen05 BF16 products, FP32 accumulation */
@@ -96,13 +96,16 @@ typedef struct {
                            the instance gets AMM_ETIMEOUT; 2e9 (about 1 s) */
   int smem_budget;      /* bytes of shared memory per block the solver may use;
                            0 = automatic */
+  int fp64_solves;      /* 1: the per-user Nr x Nr / d x d Cholesky solves of the U
+                           and W updates run in FP64 (default); 0: in FP32.  The
+                           WSR evaluation of amm_wsr is FP64 either way. */
 } amm_opts;
 
 typedef struct amm_ctx amm_ctx;
 
 /* Fill *opts with the defaults: eps1 0.1, eps2 1e-3, tc 3, gamma_c 0,
  * extrapolate 1, switch_iter -1, step_rule 0, AMM_FP32, u_at_extrapolated 0,
- * lanczos_steps 32, spin_budget 2e9, smem_budget 0. */
+ * lanczos_steps 32, spin_budget 2e9, smem_budget 0, fp64_solves 1. */
 AMM_API void amm_default_opts(amm_opts* opts);
 
 /* Create a solver for `batch` instances.  `dims` points to `n_dims` entries:

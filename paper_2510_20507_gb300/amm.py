@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
                 ("gamma_c", ctypes.c_double), ("extrapolate", ctypes.c_int), ("switch_iter", ctypes.c_int),
                 ("step_rule", ctypes.c_int), ("precision", ctypes.c_int), ("u_at_extrapolated", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
-                ("smem_budget", ctypes.c_int)]
+                ("smem_budget", ctypes.c_int), ("fp64_solves", ctypes.c_int)]
 
 
 class State(ctypes.Structure):

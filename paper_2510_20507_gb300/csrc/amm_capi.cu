@@ -13,12 +13,14 @@
 #include "amm_internal.cuh"
 
 namespace amm {
-__global__ void iterate_kernel(IterParams p);
+cudaError_t iterate_set_smem(int bytes);
+void iterate_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p);
 __global__ void normalize_kernel(const InstDesc* desc, const float2* Hin, const float* alpha, const float* sigma2,
                                  const float* P, float2* Hout, Scalars* sc);
 __global__ void init_kernel(const InstDesc* desc, const float2* V0, const float* P, float2* V, float2* Vprev,
                             Scalars* sc, float* gamma_c, int switch_iter);
-__global__ void tc_iterate_kernel(IterParams p, int prec);
+cudaError_t tc_set_smem(int bytes);
+void tc_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p, int prec);
 __global__ void wmmse_kernel(IterParams p, float bisect_tol, int bisect_max);
 int wmmse_plan_bytes(const InstDesc* desc, int batch, int budget);
 int tc_plan_bytes(const InstDesc* desc, int batch, int budget, int lanczos_steps, int prec);
@@ -119,6 +121,7 @@ extern "C" void amm_default_opts(amm_opts* o) {
   o->lanczos_steps = 32;
   o->spin_budget = 2000000000ll;  // SM clock cycles, about one second
   o->smem_budget = 0;
+  o->fp64_solves = 1;
 }
 
 static bool dims_ok(const amm_dims& d, std::string* why) {
@@ -247,9 +250,7 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
   }
   if ((e = cudaMemcpy(c->ddesc, c->hdesc.data(), sizeof(InstDesc) * batch, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(Scalars) * batch)) ||
-      (e = cudaFuncSetAttribute(amm::iterate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) ||
-      (c->tc_bytes > 0 && (e = cudaFuncSetAttribute(amm::tc_iterate_kernel,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, c->tc_bytes))) ||
+      (e = amm::iterate_set_smem(smem)) || (c->tc_bytes > 0 && (e = amm::tc_set_smem(c->tc_bytes))) ||
       (c->wm_bytes > 0 && (e = cudaFuncSetAttribute(amm::wmmse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     c->wm_bytes)))) {
     free_all(c);
@@ -324,11 +325,12 @@ static amm::IterParams base_params(amm_ctx* c) {
 }
 
 static amm_status launch_iterate(amm_ctx* c, const amm::IterParams& p) {
+  const bool f64 = c->opts.fp64_solves != 0 || p.mode == amm::kEvalWsr;  // the WSR is always FP64
   if (c->tc_bytes > 0 && p.mode != amm::kEvalWsr) {
-    amm::tc_iterate_kernel<<<c->batch, amm::kThreads, c->tc_bytes, c->stream>>>(p, c->opts.precision);
+    amm::tc_launch(f64, c->batch, c->tc_bytes, c->stream, p, c->opts.precision);
     return check_launch(c, "tc_iterate_kernel");
   }
-  amm::iterate_kernel<<<c->batch, amm::kThreads, c->smem_bytes, c->stream>>>(p);
+  amm::iterate_launch(f64, c->batch, c->smem_bytes, c->stream, p);
   return check_launch(c, "iterate_kernel");
 }
 

@@ -124,143 +124,210 @@ static __device__ __noinline__ void stage_rows(float2* dst, int sld, const float
   __syncthreads();
 }
 
-// ------------------------------------------------------- small FP64 solves
-// One thread per user.  Q: packed upper triangle (a <= b, row-major) of the
-// interference-plus-noise covariance; zo(a, s): own-stream block of Z.
-// Outputs U (NR x DD), UW = U W^{II} (NR x DD) and log det(I + M).
-template <int NR, int DD>
-__device__ bool small_solve(const float2* Qp, const float2* Zrow0, int ldz, int own0, float2* U, float2* UW,
-                            double* logdet, bool want_u) {
-  dcx L[NR][NR];
-  double inv[NR];
+// ------------------------------------------------------- small Hermitian solves
+// Complex arithmetic in the solve precision T (double by default, float on
+// request).
+template <class T>
+struct Cx {
+  T x, y;
+};
+template <class T>
+__device__ __forceinline__ Cx<T> mk(T x, T y) {
+  Cx<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <class T>
+__device__ __forceinline__ Cx<T> from2(float2 a) { return mk<T>((T)a.x, (T)a.y); }
+template <class T>
+__device__ __forceinline__ Cx<T> cj(Cx<T> a) { return mk<T>(a.x, -a.y); }
+template <class T>
+__device__ __forceinline__ Cx<T> scl(Cx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// c - a*b
+template <class T>
+__device__ __forceinline__ Cx<T> fms(Cx<T> a, Cx<T> b, Cx<T> c) {
+  return mk<T>(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+// c - a*conj(b)
+template <class T>
+__device__ __forceinline__ Cx<T> fmsj(Cx<T> a, Cx<T> b, Cx<T> c) {
+  return mk<T>(fma(-a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+// c + conj(a)*b
+template <class T>
+__device__ __forceinline__ Cx<T> jfma(Cx<T> a, Cx<T> b, Cx<T> c) {
+  return mk<T>(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+// c + a*b
+template <class T>
+__device__ __forceinline__ Cx<T> fmac(Cx<T> a, Cx<T> b, Cx<T> c) {
+  return mk<T>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+template <class T>
+__device__ __forceinline__ float2 to2(Cx<T> a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double l1p(double x) { return log1p(x); }
+__device__ __forceinline__ float l1p(float x) { return log1pf(x); }
+
+template <class T>
+__device__ __forceinline__ Cx<T> shfl4(Cx<T> v, int src) {
+  return mk<T>(__shfl_sync(0xffffffffu, v.x, src, 4), __shfl_sync(0xffffffffu, v.y, src, 4));
+}
+
+// Per-user solve by a group of 4 consecutive lanes; lane c of the group
+// owns column c of Z_own, X, U W and U (c < d), and every lane keeps the
+// small Cholesky factors.  Qp: packed upper triangle (a <= b, row-major) of
+// the interference-plus-noise covariance Q; Zrow0: the user's first row of Z
+// (row stride ldz), own-stream columns own0.. .  With L = chol(Q),
+// X = L^{-1} Z_own and M = X^H X (so that W = E^{-1} = I + M):
+//   UW = L^{-H} X = Q^{-1} Z_own,  U = UW (I+M)^{-1},
+//   logdet = log det(I + M) = sum_j log1p(pivot_j - 1), the pivots of I + M
+//   computed from M itself (no rounding of 1 + small).
+// Every lane of the warp must call this (it shuffles); `act` is false for
+// lanes without a user.  Returns false on a non-positive pivot.
+template <class T, int NR, int DD>
+__device__ bool small_solve_grp(int c, bool act, const float2* Qp, const float2* Zrow0, int ldz, int own0,
+                                float2* U, float2* UW, double* logdet, bool want_u) {
+  bool ok = act;
+  Cx<T> L[NR][NR];
+  T inv[NR];
   {
+    Cx<T> Q[NR][NR];
     int q = 0;
-    dcx Q[NR][NR];
 #pragma unroll
     for (int a = 0; a < NR; ++a)
 #pragma unroll
       for (int b = a; b < NR; ++b) {
-        Q[a][b] = dc(Qp[q++]);
-        Q[b][a] = dconj(Q[a][b]);
+        Q[a][b] = act ? from2<T>(Qp[q]) : mk<T>(a == b ? (T)1 : (T)0, (T)0);
+        Q[b][a] = cj(Q[a][b]);
+        ++q;
       }
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      double dj = Q[j][j].x;
+      T dj = Q[j][j].x;
 #pragma unroll
       for (int k = 0; k < j; ++k) dj -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
-      if (!(dj > 0.0)) return false;
-      const double rj = rsqrt(dj);
+      if (!(dj > (T)0)) {
+        ok = false;
+        dj = (T)1;
+      }
+      const T rj = rsq(dj);
       inv[j] = rj;
-      L[j][j] = dc(dj * rj, 0.0);
+      L[j][j] = mk<T>(dj * rj, (T)0);
 #pragma unroll
       for (int i = j + 1; i < NR; ++i) {
-        dcx s = Q[i][j];
+        Cx<T> s = Q[i][j];
 #pragma unroll
-        for (int k = 0; k < j; ++k) s = dfmsj(L[i][k], L[j][k], s);
-        L[i][j] = dscale(s, rj);
+        for (int k = 0; k < j; ++k) s = fmsj(L[i][k], L[j][k], s);
+        L[i][j] = scl(s, rj);
       }
     }
   }
-  // X = L^{-1} Z_own
-  dcx X[NR][DD];
+  // this lane's column of X = L^{-1} Z_own
+  const bool mine = act && c < DD;
+  Cx<T> x[NR];
 #pragma unroll
-  for (int c = 0; c < DD; ++c)
+  for (int i = 0; i < NR; ++i) {
+    Cx<T> s = mine ? from2<T>(Zrow0[(long long)i * ldz + own0 + c]) : mk<T>((T)0, (T)0);
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-      dcx s = dc(Zrow0[(long long)i * ldz + own0 + c]);
+    for (int k = 0; k < i; ++k) s = fms(L[i][k], x[k], s);
+    x[i] = scl(s, inv[i]);
+  }
+  // column c of M = X^H X: M[a][c] = sum_i conj(X[i][a]) x[i]
+  Cx<T> mcol[DD];
 #pragma unroll
-      for (int k = 0; k < i; ++k) s = dfms(L[i][k], X[k][c], s);
-      X[i][c] = dscale(s, inv[i]);
-    }
-  // I + M = I + X^H X (lower part) and its Cholesky factor R
-  dcx R[DD][DD];
-  double rinv[DD];
-  double pivprod = 1.0;
+  for (int a = 0; a < DD; ++a) {
+    Cx<T> s = mk<T>((T)0, (T)0);
+#pragma unroll
+    for (int i = 0; i < NR; ++i) s = jfma(shfl4(x[i], a), x[i], s);
+    mcol[a] = s;
+  }
+  // every lane gathers M and factors I + M = R R^H
+  Cx<T> R[DD][DD];
+  T rinv[DD];
+  T mypiv = (T)0;
   {
-    dcx A[DD][DD];
+    Cx<T> A[DD][DD];
 #pragma unroll
-    for (int a = 0; a < DD; ++a)
+    for (int b = 0; b < DD; ++b)
 #pragma unroll
-      for (int b = 0; b <= a; ++b) {
-        dcx s = dc(a == b ? 1.0 : 0.0, 0.0);
-#pragma unroll
-        for (int i = 0; i < NR; ++i) s = djfma(X[i][a], X[i][b], s);
-        A[a][b] = s;  // (X^H X)[a][b] = sum_i conj(X[i][a]) X[i][b]
-      }
+      for (int a = 0; a < DD; ++a) A[a][b] = shfl4(mcol[a], b);
 #pragma unroll
     for (int j = 0; j < DD; ++j) {
-      double dj = A[j][j].x;
+      T dm1 = A[j][j].x;  // pivot - 1
 #pragma unroll
-      for (int k = 0; k < j; ++k) dj -= R[j][k].x * R[j][k].x + R[j][k].y * R[j][k].y;
-      if (!(dj > 0.0)) return false;
-      pivprod *= dj;
-      const double rj = rsqrt(dj);
+      for (int k = 0; k < j; ++k) dm1 -= R[j][k].x * R[j][k].x + R[j][k].y * R[j][k].y;
+      if (!(dm1 > (T)-1)) {
+        ok = false;
+        dm1 = (T)0;
+      }
+      if (j == c) mypiv = dm1;
+      const T dj = (T)1 + dm1;
+      const T rj = rsq(dj);
       rinv[j] = rj;
-      R[j][j] = dc(dj * rj, 0.0);
+      R[j][j] = mk<T>(dj * rj, (T)0);
 #pragma unroll
       for (int i = j + 1; i < DD; ++i) {
-        dcx s = A[i][j];
+        Cx<T> s = A[i][j];
 #pragma unroll
-        for (int k = 0; k < j; ++k) s = dfmsj(R[i][k], R[j][k], s);
-        R[i][j] = dscale(s, rj);
+        for (int k = 0; k < j; ++k) s = fmsj(R[i][k], R[j][k], s);
+        R[i][j] = scl(s, rj);
       }
     }
   }
-  *logdet = log(pivprod);
-  if (!want_u) return true;
-  // UW = L^{-H} X = Q^{-1} Z_own
-  dcx Y[NR][DD];
+  // log det(I + M): lane c contributes log1p of pivot c, summed over the group
+  double ld = (c < DD) ? (double)l1p(mypiv) : 0.0;
+  ld += __shfl_xor_sync(0xffffffffu, ld, 1, 4);
+  ld += __shfl_xor_sync(0xffffffffu, ld, 2, 4);
+  if (c == 0) *logdet = ld;
+  if (!want_u) return ok;
+  // this lane's column of UW = L^{-H} x
+  Cx<T> y[NR];
 #pragma unroll
-  for (int c = 0; c < DD; ++c)
+  for (int i = NR - 1; i >= 0; --i) {
+    Cx<T> s = x[i];
 #pragma unroll
-    for (int i = NR - 1; i >= 0; --i) {
-      dcx s = X[i][c];
+    for (int k = i + 1; k < NR; ++k) s = fms(cj(L[k][i]), y[k], s);
+    y[i] = scl(s, inv[i]);
+  }
+  // column c of (I+M)^{-1}: R g = e_c, then R^H m = g
+  Cx<T> g[DD], mi[DD];
 #pragma unroll
-      for (int k = i + 1; k < NR; ++k) s = dfms(dconj(L[k][i]), Y[k][c], s);
-      Y[i][c] = dscale(s, inv[i]);
-    }
-  // (I+M)^{-1} = R^{-H} R^{-1}: Rinv lower triangular
-  dcx Ri[DD][DD];
+  for (int i = 0; i < DD; ++i) {
+    Cx<T> s = mk<T>(i == c ? (T)1 : (T)0, (T)0);
 #pragma unroll
-  for (int j = 0; j < DD; ++j) {
-    Ri[j][j] = dc(rinv[j], 0.0);
+    for (int k = 0; k < i; ++k) s = fms(R[i][k], g[k], s);
+    g[i] = scl(s, rinv[i]);
+  }
 #pragma unroll
-    for (int i = j + 1; i < DD; ++i) {
-      dcx s = dc(0.0, 0.0);
+  for (int i = DD - 1; i >= 0; --i) {
+    Cx<T> s = g[i];
 #pragma unroll
-      for (int k = j; k < i; ++k) s = dfms(R[i][k], Ri[k][j], s);
-      Ri[i][j] = dscale(s, rinv[i]);
+    for (int k = i + 1; k < DD; ++k) s = fms(cj(R[k][i]), mi[k], s);
+    mi[i] = scl(s, rinv[i]);
+  }
+  // U[:, c] = sum_b UW[:, b] (I+M)^{-1}[b][c]
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    Cx<T> s = mk<T>((T)0, (T)0);
+#pragma unroll
+    for (int b = 0; b < DD; ++b) s = fmac(shfl4(y[i], b), mi[b], s);
+    if (mine && ok) {
+      U[i * DD + c] = to2(s);
+      UW[i * DD + c] = to2(y[i]);
     }
   }
-  dcx Mi[DD][DD];
-#pragma unroll
-  for (int a = 0; a < DD; ++a)
-#pragma unroll
-    for (int b = 0; b < DD; ++b) {
-      dcx s = dc(0.0, 0.0);
-      const int k0 = a > b ? a : b;
-#pragma unroll
-      for (int k = 0; k < DD; ++k)
-        if (k >= k0) s = djfma(Ri[k][a], Ri[k][b], s);
-      Mi[a][b] = s;
-    }
-#pragma unroll
-  for (int i = 0; i < NR; ++i)
-#pragma unroll
-    for (int c = 0; c < DD; ++c) {
-      dcx s = dc(0.0, 0.0);
-#pragma unroll
-      for (int b = 0; b < DD; ++b) s = dfma(Y[i][b], Mi[b][c], s);
-      U[i * DD + c] = tof(s);
-      UW[i * DD + c] = tof(Y[i][c]);
-    }
-  return true;
+  return ok;
 }
 
-static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, const float2* Qp, const float2* Zrow0, int ldz, int own0,
-                                     float2* U, float2* UW, double* logdet, bool want_u) {
+template <class T>
+static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, bool act, const float2* Qp,
+                                                         const float2* Zrow0, int ldz, int own0, float2* U,
+                                                         float2* UW, double* logdet, bool want_u) {
 #define AMM_SS(a, b) \
-  if (Nr == a && d == b) return small_solve<a, b>(Qp, Zrow0, ldz, own0, U, UW, logdet, want_u);
+  if (Nr == a && d == b) return small_solve_grp<T, a, b>(c, act, Qp, Zrow0, ldz, own0, U, UW, logdet, want_u);
   AMM_SS(1, 1)
   AMM_SS(2, 1) AMM_SS(2, 2)
   AMM_SS(3, 1) AMM_SS(3, 2) AMM_SS(3, 3)
@@ -470,17 +537,25 @@ __device__ __forceinline__ void covariance_phase(const InstDesc& D, const Layout
 // S3b/S4: FP64 solves, one thread per user, then rho = sum alpha_r R_r
 // (block-uniform).  own-stream block of user r: rows r*Nr.., columns own0..
 // of the Z view (zrow0(r) gives row r*Nr, ldz its row stride).
+template <class T>
 __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& Ly, const float2* Z, int ldz,
                                               const float2* sQ, float2* sU, float2* sUW, double* sRho,
                                               const float* alpha_u, bool want_u, double* red, int* fail) {
   const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, np = Ly.np, CK = Ly.CK;
-  for (int r = threadIdx.x; r < CK; r += blockDim.x) {
+  // four lanes per user; the trip count is warp-uniform (the solve shuffles)
+  for (int base = 0; base < 4 * CK; base += blockDim.x) {
+    const int e = base + threadIdx.x;
+    const bool act = e < 4 * CK;
+    const int r = act ? e >> 2 : 0, c = e & 3;
+    if (!__any_sync(0xffffffffu, act)) continue;  // warps without a user skip the (FP64) solve
     const int own0 = (r / K) * n + (r % K) * d;
     double ld = 0.0;
-    const bool ok = small_solve_dispatch(Nr, d, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
-                                         sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u);
-    if (!ok || !isfinite(ld)) atomicExch(fail, kNumeric);
-    sRho[r] = ok ? ld : 0.0;
+    const bool ok = small_solve_dispatch<T>(Nr, d, c, act, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
+                                            sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u);
+    if (act && c == 0) {
+      if (!ok || !isfinite(ld)) atomicExch(fail, kNumeric);
+      sRho[r] = ok ? ld : 0.0;
+    }
   }
   __syncthreads();
   double part = 0.0;

@@ -154,31 +154,6 @@ __device__ __forceinline__ float2 cjfma(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
-struct dcx { double x, y; };
-__device__ __forceinline__ dcx dc(double x, double y) { dcx r; r.x = x; r.y = y; return r; }
-__device__ __forceinline__ dcx dc(float2 a) { return dc((double)a.x, (double)a.y); }
-__device__ __forceinline__ dcx dadd(dcx a, dcx b) { return dc(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ dcx dsub(dcx a, dcx b) { return dc(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ dcx dscale(dcx a, double s) { return dc(a.x * s, a.y * s); }
-__device__ __forceinline__ dcx dconj(dcx a) { return dc(a.x, -a.y); }
-// c - a*b
-__device__ __forceinline__ dcx dfms(dcx a, dcx b, dcx c) {
-  return dc(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
-}
-// c - a*conj(b)
-__device__ __forceinline__ dcx dfmsj(dcx a, dcx b, dcx c) {
-  return dc(fma(-a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
-}
-// c + conj(a)*b
-__device__ __forceinline__ dcx djfma(dcx a, dcx b, dcx c) {
-  return dc(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
-}
-// c + a*b
-__device__ __forceinline__ dcx dfma(dcx a, dcx b, dcx c) {
-  return dc(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
-}
-__device__ __forceinline__ float2 tof(dcx a) { return make_float2((float)a.x, (float)a.y); }
-
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -27,6 +27,7 @@
 namespace amm {
 
 // ------------------------------------------------------------------ kernel
+template <class T>
 __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t mbar;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     covariance_phase(D, Ly, [&](int row, int c) { return Zc[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
     // ---- S3b/S4: FP64 small solves, one thread per user; rho = WSR(V^{t-1})
-    rho = solve_phase(D, Ly, Zc, ldz, sQ, sU, sUW, sRho, alpha_u, p.mode != kEvalWsr, red, &s_fail);
+    rho = solve_phase<T>(D, Ly, Zc, ldz, sQ, sU, sUW, sRho, alpha_u, p.mode != kEvalWsr, red, &s_fail);
     if (s_fail != kOk) break;
     if (p.mode == kEvalWsr) {
       if (tid == 0) p.wsr_out[b] = rho / 0.69314718055994530942;
@@ -270,6 +271,17 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     }
     scg->status = s_fail;
   }
+}
+
+// Host-side launchers (the capi translation unit does not see the templates).
+cudaError_t iterate_set_smem(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(iterate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(iterate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+void iterate_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p) {
+  if (fp64) iterate_kernel<double><<<grid, kThreads, smem, st>>>(p);
+  else iterate_kernel<float><<<grid, kThreads, smem, st>>>(p);
 }
 
 // ------------------------------------------------------------------ set-up kernels

@@ -59,6 +59,7 @@ __host__ __device__ inline TcLayout plan_tc(const InstDesc& D, int budget, int l
   return T;
 }
 
+template <class SolveT>
 __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, int prec) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t mbar;
@@ -66,7 +67,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   __shared__ int s_fail;
   __shared__ int s_ctrl[8];
   __shared__ float s_bcast;
-  __shared__ float s_scale;
 
   const int b = blockIdx.x;
   const InstDesc D = p.desc[b];
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     // ---- S3/S4: covariance, FP64 solves, rho = WSR(V^{t-1}), stage test
     covariance_phase(D, Ly, [&](int row, int c) { return Zs[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
-    rho = solve_phase(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true, red, &s_fail);
+    rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true, red, &s_fail);
     if (s_fail != kOk) break;
     if (tid == 0)
       stage_logic(s_ctrl, rho, scg->rho_prev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
@@ -425,6 +425,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     }
     scg->status = st;
   }
+}
+
+cudaError_t tc_set_smem(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(tc_iterate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_iterate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+void tc_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p, int prec) {
+  if (fp64) tc_iterate_kernel<double><<<grid, kThreads, smem, st>>>(p, prec);
+  else tc_iterate_kernel<float><<<grid, kThreads, smem, st>>>(p, prec);
 }
 
 // Host-side query: can every instance of the batch use the tensor-core

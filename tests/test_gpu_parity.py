@@ -169,7 +169,8 @@ def test_option_variants(opt):
     g.warmstart()
     g.step(iters)
     got = g.wsr()
-    oopt = {k: (bool(v) if k == "extrapolate" else v) for k, v in opt.items()}
+    names = {"tc": "Tc"}
+    oopt = {names.get(k, k): (bool(v) if k == "extrapolate" else v) for k, v in opt.items()}
     for b, inst in enumerate(insts):
         ref = oracle_run(inst, iters, **oopt)
         if "switch_iter" not in opt and switch_margin(ref) < 1e-4:
@@ -299,4 +300,32 @@ def test_wmmse_step_matches_oracle(shape):
                                tol=1e-4, max_bisect=100)
         want = hist[-1] / np.log(2.0)
         assert abs(got[b] - want) <= WSR_TOL * want, (shape, b, got[b], want)
+    g.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 16, 64, 4, 4), (2, 3, 17, 3, 2), (1, 5, 33, 4, 3)])
+def test_teacher_forced_step_fp32_solves(shape):
+    """fp64_solves = 0: the per-user Cholesky solves in FP32 (log-det from
+    log1p of the pivots of I + M computed from M) still reproduce the
+    oracle's step within 1e-5."""
+    n, iters = 4, 10
+    insts = small_batch(shape, n, 8000 + sum(shape))
+    opt = osv.Options()
+    runs = [_oracle_states(inst, iters, opt) for inst in insts]
+    g = GpuRun(insts, fp64_solves=0)
+    worst = 0.0
+    for t in range(iters):
+        states = [r[0][t] for r in runs]
+        g.set_state_from_oracle(states)
+        g.step(1)
+        Vs = g.V()
+        for b in range(n):
+            if t > 0 and states[b].stage == 1:
+                relchg = abs(runs[b][2][t].rho - runs[b][2][t - 1].rho) / abs(runs[b][2][t - 1].rho)
+                if abs(relchg - opt.eps1) < 1e-4:
+                    continue
+            e = rel(Vs[b], runs[b][1][t])
+            worst = max(worst, e)
+            assert e <= STEP_TOL, (shape, b, t + 1, e)
+    print(f"fp32 solves {shape}: teacher-forced worst rel err {worst:.2e}")
     g.close()

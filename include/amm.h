@@ -63,7 +63,9 @@ typedef enum {
 typedef enum {
   AMM_FP32 = 0,    /* CUDA-core FP32 FFMA GEMMs (the plain path) */
   AMM_BF16 = 1,    /* tcgen05 BF16 products, FP32 accumulation */
-  AMM_BF16X3 = 2   /* tcgen05 split BF16: hi*hi + hi*lo + lo*hi, FP32 accumulation */
+  AMM_BF16X3 = 2,  /* tcgen05 split BF16: hi*hi + hi*lo + lo*hi, FP32 accumulation */
+  AMM_BF16X6 = 3   /* tcgen05 three-term split (hi + mid + lo), six products, about
+                      FP32 accuracy */
 } amm_precision;
 
 /* Sizes of one instance.  1 <= cells <= 16, users >= 1, d <= nr <= 4. */

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libamm.so")
 AMM_OK, AMM_EINVAL, AMM_ENOMEM, AMM_ECUDA, AMM_ENUMERIC, AMM_ETIMEOUT, AMM_ENOTCONV, AMM_EUNSUPPORTED = range(8)
 STATUS_NAMES = {0: "AMM_OK", 1: "AMM_EINVAL", 2: "AMM_ENOMEM", 3: "AMM_ECUDA", 4: "AMM_ENUMERIC",
                 5: "AMM_ETIMEOUT", 6: "AMM_ENOTCONV", 7: "AMM_EUNSUPPORTED"}
-PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
 
 
 class AmmError(RuntimeError):

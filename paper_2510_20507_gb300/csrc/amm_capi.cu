@@ -166,7 +166,7 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
   amm_opts o;
   amm_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision != AMM_FP32 && o.precision != AMM_BF16 && o.precision != AMM_BF16X3)
+  if (o.precision != AMM_FP32 && o.precision != AMM_BF16 && o.precision != AMM_BF16X3 && o.precision != AMM_BF16X6)
     return fail(nullptr, AMM_EINVAL, "unknown precision");
   if (o.u_at_extrapolated) return fail(nullptr, AMM_EUNSUPPORTED, "u_at_extrapolated = 1 is not implemented");
   if (o.step_rule < 0 || o.step_rule > 2 || o.tc < 0 || !(o.eps1 >= 0) || !(o.eps2 >= 0))

@@ -22,10 +22,19 @@
 
 namespace amm {
 
+// Number of bf16 terms each FP32 operand is split into: 1 (BF16), 2 (hi + lo,
+// products hi*hi + hi*lo + lo*hi) or 3 (hi + mid + lo, products hi*hi +
+// hi*mid + mid*hi + mid*mid + hi*lo + lo*hi, about FP32 accuracy).
+__host__ __device__ inline int tc_splits(int prec) { return prec == 3 ? 3 : (prec == 2 ? 2 : 1); }
+// With three terms the gradient GEMM reads H_real^T as the MN-major view of
+// the forward operand instead of keeping a K-major copy.
+__host__ __device__ inline bool tc_mn_gradient(int prec) { return prec == 3; }
+
 struct TcLayout {
   Layout base;  // the small per-user region (offsets from the plain plan)
-  int K1p, K2p, Np, Bk, ncols;
-  int off_A1h, off_A1l, off_A2h, off_A2l, off_Bh, off_Bl, off_Zs, off_L;
+  int K1p, K2p, Np, Bk, ncols, ns;
+  bool mn;
+  int off_A1[3], off_A2[3], off_B[3], off_Zs, off_L, end_ops;
   int total;
   bool ok;
 };
@@ -34,21 +43,30 @@ __host__ __device__ inline TcLayout plan_tc(const InstDesc& D, int budget, int l
   TcLayout T;
   T.base = plan_layout(D, 0, lanczos_steps);  // budget 0: only the small region
   const int m = T.base.m, n = T.base.n;
-  T.K1p = align_up(2 * D.Nt, 16);
+  T.ns = tc_splits(prec);
+  T.mn = tc_mn_gradient(prec);
+  // the MN-major view spans all 128 rows of the gradient tile: keep K1 at 128
+  T.K1p = T.mn ? 128 : align_up(2 * D.Nt, 16);
   T.K2p = align_up(2 * m, 16);
   T.Np = align_up(n < 16 ? 16 : n, 16);
   T.Bk = T.K1p > T.K2p ? T.K1p : T.K2p;
   int need = 5 * T.Np;
   T.ncols = 32;
   while (T.ncols < need) T.ncols <<= 1;
-  const bool x3 = (prec == 2);
   int off = align_up(T.base.total, 1024);
-  T.off_A1h = off; off += 128 * T.K1p * 2;
-  T.off_A1l = off; off += x3 ? 128 * T.K1p * 2 : 0;
-  T.off_A2h = off; off += 128 * T.K2p * 2;
-  T.off_A2l = off; off += x3 ? 128 * T.K2p * 2 : 0;
-  T.off_Bh = off;  off += T.Np * T.Bk * 2;
-  T.off_Bl = off;  off += x3 ? T.Np * T.Bk * 2 : 0;
+  for (int s = 0; s < 3; ++s) {
+    T.off_A1[s] = off;
+    if (s < T.ns) off += 128 * T.K1p * 2;
+  }
+  for (int s = 0; s < 3; ++s) {
+    T.off_A2[s] = off;
+    if (s < T.ns && !T.mn) off += 128 * T.K2p * 2;
+  }
+  for (int s = 0; s < 3; ++s) {
+    T.off_B[s] = off;
+    if (s < T.ns) off += T.Np * T.Bk * 2;
+  }
+  T.end_ops = off;
   T.off_Zs = off;  off += m * T.base.ldz * 8;
   off = align_up(off, 16);
   const int szL = (T.base.Lm + 1) * D.Nt * 8;
@@ -76,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   const TcLayout T = plan_tc(D, p.smem_budget, p.lanczos_steps, prec);
   const Layout& Ly = T.base;
   const int m = Ly.m, n = Ly.n, ldz = Ly.ldz;
-  const bool x3 = (prec == 2);
+  const int NS = T.ns;
 
   if (tid == 0) {
     const int st = scg->status;
@@ -106,12 +124,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   float* ta = reinterpret_cast<float*>(smem + Ly.off_tri);
   float* tb = ta + (Ly.Lm + 1);
   float2* lh = reinterpret_cast<float2*>(smem + Ly.off_h);
-  unsigned char* A1h = smem + T.off_A1h;
-  unsigned char* A1l = smem + T.off_A1l;
-  unsigned char* A2h = smem + T.off_A2h;
-  unsigned char* A2l = smem + T.off_A2l;
-  unsigned char* Bh = smem + T.off_Bh;
-  unsigned char* Bl = smem + T.off_Bl;
+  unsigned char* A1[3] = {smem + T.off_A1[0], smem + T.off_A1[1], smem + T.off_A1[2]};
+  unsigned char* A2[3] = {smem + T.off_A2[0], smem + T.off_A2[1], smem + T.off_A2[2]};
+  unsigned char* Bs[3] = {smem + T.off_B[0], smem + T.off_B[1], smem + T.off_B[2]};
   float2* Zs = reinterpret_cast<float2*>(smem + T.off_Zs);
   float2* QL = (T.off_L >= 0) ? reinterpret_cast<float2*>(smem + T.off_L) : p.Lws + D.l_off;
 
@@ -124,8 +139,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
 
   // ---- zero the operand buffers (padding rows / K columns must read as 0)
   {
-    uint4* z4 = reinterpret_cast<uint4*>(smem + T.off_A1h);
-    const int n4 = (T.off_Zs - T.off_A1h) / 16;
+    uint4* z4 = reinterpret_cast<uint4*>(smem + T.off_A1[0]);
+    const int n4 = (T.end_ops - T.off_A1[0]) / 16;
     for (int e = tid; e < n4; e += blockDim.x) z4[e] = make_uint4(0u, 0u, 0u, 0u);
   }
   tc::fence_before_sync();
@@ -137,27 +152,37 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   const unsigned colD2 = 2u * Np;
   const unsigned colV[2] = {3u * Np, 4u * Np};
 
+  // split x into NS bf16 terms
+  auto split = [&](float x, __nv_bfloat16* t) {
+    t[0] = __float2bfloat16_rn(x);
+    float r = x - __bfloat162float(t[0]);
+    if (NS > 1) {
+      t[1] = __float2bfloat16_rn(r);
+      r -= __bfloat162float(t[1]);
+    }
+    if (NS > 2) t[2] = __float2bfloat16_rn(r);
+  };
+  auto put = [&](unsigned char* const* Ar, int row, int k, int Kp, const __nv_bfloat16* t, bool neg) {
+    for (int q = 0; q < NS; ++q)
+      *reinterpret_cast<__nv_bfloat16*>(Ar[q] + tc::kmaj_off(row, k, Kp)) = neg ? __hneg(t[q]) : t[q];
+  };
   // ---- A operands from the normalised channel
   for (int e = tid; e < m * Nt; e += blockDim.x) {
     const int i = e / Nt, q = e - i * Nt;
     const float2 h = Hg[e];
-    __nv_bfloat16 rh, rl, ih, il;
-    tc::split_bf16(h.x, rh, rl);
-    tc::split_bf16(h.y, ih, il);
-    const __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
-    auto put = [&](unsigned char* Ah, unsigned char* Al, int row, int k, int Kp, __nv_bfloat16 vh,
-                   __nv_bfloat16 vl) {
-      *reinterpret_cast<__nv_bfloat16*>(Ah + tc::kmaj_off(row, k, Kp)) = vh;
-      if (x3) *reinterpret_cast<__nv_bfloat16*>(Al + tc::kmaj_off(row, k, Kp)) = vl;
-    };
-    put(A1h, A1l, i, q, T.K1p, rh, rl);            // Hr
-    put(A1h, A1l, i, Nt + q, T.K1p, nih, nil);     // -Hi
-    put(A1h, A1l, m + i, q, T.K1p, ih, il);        // Hi
-    put(A1h, A1l, m + i, Nt + q, T.K1p, rh, rl);   // Hr
-    put(A2h, A2l, q, i, T.K2p, rh, rl);            // Hr^T
-    put(A2h, A2l, q, m + i, T.K2p, ih, il);        // Hi^T
-    put(A2h, A2l, Nt + q, i, T.K2p, nih, nil);     // -Hi^T
-    put(A2h, A2l, Nt + q, m + i, T.K2p, rh, rl);   // Hr^T
+    __nv_bfloat16 rt[3], it[3];
+    split(h.x, rt);
+    split(h.y, it);
+    put(A1, i, q, T.K1p, rt, false);           // Hr
+    put(A1, i, Nt + q, T.K1p, it, true);       // -Hi
+    put(A1, m + i, q, T.K1p, it, false);       // Hi
+    put(A1, m + i, Nt + q, T.K1p, rt, false);  // Hr
+    if (!T.mn) {
+      put(A2, q, i, T.K2p, rt, false);           // Hr^T
+      put(A2, q, m + i, T.K2p, it, false);       // Hi^T
+      put(A2, Nt + q, i, T.K2p, it, true);       // -Hi^T
+      put(A2, Nt + q, m + i, T.K2p, rt, false);  // Hr^T
+    }
   }
 
   // lane-owner mapping of the tensor-memory rows: warp w reads lanes of
@@ -193,35 +218,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
         for (int j = 0; j < 16; ++j) {
           const int c = cc * 16 + j;
           if (c < n) {
-            __nv_bfloat16 hi, lo;
-            tc::split_bf16(v[j], hi, lo);
-            *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, R, T.K1p)) = hi;
-            if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, R, T.K1p)) = lo;
+            __nv_bfloat16 t[3];
+            split(v[j], t);
+            put(Bs, c, R, T.K1p, t, false);
           }
         }
       }
     }
   };
   unsigned phase = 0;
-  auto gemm = [&](unsigned dcol, unsigned char* Ahi, unsigned char* Alo, int Kp) -> bool {
+  // the products of the split terms: (a-term, b-term)
+  const int npairs = (NS == 1) ? 1 : (NS == 2 ? 3 : 6);
+  const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+  // D = A * B over Kp; mn: A is the MN-major view of the forward operand (H_real^T)
+  auto gemm = [&](unsigned dcol, unsigned char* const* Ar, int Kp, bool mn) -> bool {
     // operands written by the threads -> visible to the tensor core
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t idesc = tc::idesc_bf16(128, Np);
-      const unsigned sbo = (unsigned)(Kp / 8) * 128u;
-      const unsigned ah = tc::su32(Ahi), al = tc::su32(Alo), bh = tc::su32(Bh), bl = tc::su32(Bl);
+      const uint32_t idesc = tc::idesc_bf16(128, Np) | (mn ? (1u << 15) : 0u);
+      const unsigned sbo_b = (unsigned)(Kp / 8) * 128u;
+      const unsigned sbo_a = mn ? (unsigned)(T.K1p / 8) * 128u : sbo_b;
       for (int kk = 0; kk < Kp / 16; ++kk) {
-        const unsigned off = (unsigned)kk * 256u;
-        tc::mma_bf16(tbase + dcol, tc::smem_desc(ah + off, 128u, sbo), tc::smem_desc(bh + off, 128u, sbo), idesc,
-                     kk > 0);
-        if (x3) {
-          tc::mma_bf16(tbase + dcol, tc::smem_desc(ah + off, 128u, sbo), tc::smem_desc(bl + off, 128u, sbo), idesc,
-                       1u);
-          tc::mma_bf16(tbase + dcol, tc::smem_desc(al + off, 128u, sbo), tc::smem_desc(bh + off, 128u, sbo), idesc,
-                       1u);
+        const unsigned aoff = mn ? (unsigned)kk * 2u * sbo_a : (unsigned)kk * 256u;
+        const unsigned boff = (unsigned)kk * 256u;
+        for (int q = 0; q < npairs; ++q) {
+          tc::mma_bf16(tbase + dcol, tc::smem_desc(tc::su32(Ar[pa[q]]) + aoff, 128u, sbo_a),
+                       tc::smem_desc(tc::su32(Bs[pb[q]]) + boff, 128u, sbo_b), idesc, (kk > 0 || q > 0) ? 1u : 0u);
         }
       }
       tc::commit(&mbar);
@@ -245,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   tc::fence_after_sync();
   if (p.extrapolate && s_ctrl[0] >= 3) {
     write_B1(colV[1]);
-    gemm(colD1[1], A1h, A1l, T.K1p);  // Z(V^{t-2})
+    gemm(colD1[1], A1, T.K1p, false);  // Z(V^{t-2})
   }
   write_B1(colV[0]);
 
@@ -254,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     const int t = s_ctrl[0];
     const float omega = (p.extrapolate && t >= 3) ? (float)(t - 2) / (float)(t + 1) : 0.f;
     // ---- S2: Z = H V^{t-1} on the tensor cores
-    if (!gemm(colD1[zc], A1h, A1l, T.K1p)) break;
+    if (!gemm(colD1[zc], A1, T.K1p, false)) break;
     // accumulator -> FP32 Z in shared memory (lane R < m: Re row R; m <= R < 2m: Im row R - m)
     for (int cc = half; cc < nchunks; cc += 2) {
       float v[16];
@@ -301,18 +326,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     gradient_rhs_phase(
         D, Ly, [&](int row, int c) { return Zs[(long long)row * ldz + c]; }, sU, sP, alpha_u,
         [&](int row, int c, float2 y) {
-          __nv_bfloat16 hi, lo;
-          tc::split_bf16(y.x, hi, lo);
-          *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, row, T.K2p)) = hi;
-          if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, row, T.K2p)) = lo;
-          tc::split_bf16(y.y, hi, lo);
-          *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, m + row, T.K2p)) = hi;
-          if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, m + row, T.K2p)) = lo;
+          __nv_bfloat16 t[3];
+          split(y.x, t);
+          put(Bs, c, row, T.K2p, t, false);
+          split(y.y, t);
+          put(Bs, c, m + row, T.K2p, t, false);
         });
     for (int e = tid; e < n * (T.K2p - 2 * m); e += blockDim.x) {  // K padding of B2
       const int c = e / (T.K2p - 2 * m), k = 2 * m + e % (T.K2p - 2 * m);
-      *reinterpret_cast<__nv_bfloat16*>(Bh + tc::kmaj_off(c, k, T.K2p)) = __float2bfloat16_rn(0.f);
-      if (x3) *reinterpret_cast<__nv_bfloat16*>(Bl + tc::kmaj_off(c, k, T.K2p)) = __float2bfloat16_rn(0.f);
+      const __nv_bfloat16 z[3] = {__float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f)};
+      put(Bs, c, k, T.K2p, z, false);
     }
     __syncthreads();
     // ---- S5: step size, eq. (16); Lanczos reads H back from the split operand
@@ -323,13 +346,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
         const float lam = lanczos_norm(
             D, Ly,
             [&](int i, int q) {
-              float re = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1h + tc::kmaj_off(i, q, T.K1p)));
-              float im =
-                  __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1h + tc::kmaj_off(m + i, q, T.K1p)));
-              if (x3) {
-                re += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1l + tc::kmaj_off(i, q, T.K1p)));
+              float re = 0.f, im = 0.f;
+              for (int t = NS - 1; t >= 0; --t) {  // small terms first
+                re += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(i, q, T.K1p)));
                 im += __bfloat162float(
-                    *reinterpret_cast<const __nv_bfloat16*>(A1l + tc::kmaj_off(m + i, q, T.K1p)));
+                    *reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(m + i, q, T.K1p)));
               }
               return make_float2(re, im);
             },
@@ -342,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       if (tid == 0) cellf[0] = gk;
     }
     // ---- S6/S7: G = H^H Y on the tensor cores
-    if (!gemm(colD2, A2h, A2l, T.K2p)) break;
+    if (!gemm(colD2, T.mn ? A1 : A2, T.K2p, T.mn)) break;
     const float gj = cellf[0];
     float nrm = 0.f;
     for (int cc = half; cc < nchunks; cc += 2) {

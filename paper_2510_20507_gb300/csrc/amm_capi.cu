@@ -250,9 +250,12 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
   }
   if ((e = cudaMemcpy(c->ddesc, c->hdesc.data(), sizeof(InstDesc) * batch, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(Scalars) * batch)) ||
-      (e = amm::iterate_set_smem(smem)) || (c->tc_bytes > 0 && (e = amm::tc_set_smem(c->tc_bytes))) ||
+      // the limit is per kernel, not per context: raise it to the largest budget any
+      // context may use so that contexts of different sizes can coexist
+      (e = amm::iterate_set_smem(amm::kSmemMax - 1024)) ||
+      (c->tc_bytes > 0 && (e = amm::tc_set_smem(amm::kSmemMax - 1024))) ||
       (c->wm_bytes > 0 && (e = cudaFuncSetAttribute(amm::wmmse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    c->wm_bytes)))) {
+                                                    amm::kSmemMax - 1024)))) {
     free_all(c);
     delete c;
     return fail(nullptr, AMM_ECUDA, std::string("set-up failed: ") + cudaGetErrorString(e));

@@ -329,3 +329,19 @@ def test_teacher_forced_step_fp32_solves(shape):
             assert e <= STEP_TOL, (shape, b, t + 1, e)
     print(f"fp32 solves {shape}: teacher-forced worst rel err {worst:.2e}")
     g.close()
+
+
+def test_contexts_of_different_sizes_coexist():
+    """A small context created after a large one must not shrink the large
+    one's shared-memory allowance."""
+    big = wl.single_cell_64(first=0, count=4)
+    small = wl.tiny_fp64(4)
+    a = GpuRun(big)
+    b = GpuRun(small)
+    a.warmstart()
+    a.step(3)
+    b.warmstart()
+    b.step(3)
+    assert np.all(np.isfinite(a.wsr())) and np.all(np.isfinite(b.wsr()))
+    a.close()
+    b.close()

@@ -204,6 +204,36 @@ AMM_API amm_status amm_solve_host(amm_ctx* ctx, const void* H, const float* alph
                           const float* sigma2, const float* P, const void* V0,
                           int n_iters, double* wsr_out, void* V_out);
 
+/* A whole solve without any device allocation, for callers that must not
+ * allocate device memory while they run: a base-station scheduler computing
+ * precoders inside a per-slot deadline, where cudaMalloc / cudaFree can
+ * synchronise the device and stall far longer than the slot lasts, or a
+ * process whose own pool owns all device memory.  (The paper has no
+ * counterpart: this is a deployment entry point.)
+ *
+ * Runs, on a uniform batch of `batch` instances of sizes *dims, what
+ * amm_set_problem + amm_warmstart(V0) + amm_step(n_iters) + amm_wsr do on the
+ * FP32 GEMM path, with the same kernels and results.  Inputs H, alpha, sigma2,
+ * P, V0 and outputs V_out (final precoders, complex64, V layout) and wsr_out
+ * (double per instance, bits; NaN for an instance with non-finite input or a
+ * failed factorisation) are caller-owned device buffers.  The workspace lives
+ * in one static device array of 32 MiB that every GPU loading the library
+ * holds until the process exits; batches needing more get AMM_EINVAL with
+ * the byte count in `err` (a caller buffer of err_len bytes, may be NULL).
+ * opts may be NULL; its precision must be AMM_FP32.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call reuses the array and overwrites or clears what it
+ * reads, so consecutive calls are independent; calls whose GPU work overlaps
+ * (two host threads, or two streams) race on the array and must not be
+ * issued.  Asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ * stream). */
+AMM_API amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const amm_opts* opts, const void* H,
+                                     const float* alpha, const float* sigma2, const float* P, const void* V0,
+                                     int n_iters, void* V_out, double* wsr_out, void* stream, char* err,
+                                     int err_len);
+
 /* Release the context and its workspace (synchronises its stream). */
 AMM_API void amm_destroy(amm_ctx* ctx);
 

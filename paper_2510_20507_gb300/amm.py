@@ -47,7 +47,8 @@ class State(ctypes.Structure):
 
 EXPORTS = ["amm_default_opts", "amm_create", "amm_sizes", "amm_set_problem", "amm_warmstart", "amm_step",
            "amm_solve", "amm_wsr", "amm_wmmse_step", "amm_get_V", "amm_get_state", "amm_set_state",
-           "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count"]
+           "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count",
+           "amm_solve_noalloc"]
 
 _lib = None
 
@@ -81,6 +82,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "amm_destroy": (None, [vp]),
         "amm_last_error": (ctypes.c_char_p, [vp]),
         "amm_launch_count": (i64, [vp]),
+        "amm_solve_noalloc": (i32, [i32, ctypes.POINTER(Dims), ctypes.POINTER(Opts), vp, vp, vp, vp, vp, i32, vp,
+                                    vp, vp, ctypes.c_char_p, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -117,6 +120,23 @@ def _stream_handle(stream) -> Optional[int]:
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def solve_noalloc(batch, dims, H, alpha, sigma2, P, V0, n_iters, V_out, wsr_out, opts=None, stream=None):
+    """amm_solve_noalloc: a whole solve that allocates no device memory (its
+    workspace is a static device array inside the library), for callers that
+    may not allocate device memory while they run.  All tensors are
+    caller-owned device buffers in the C-ABI layouts."""
+    lib = load_library()
+    if opts is None:
+        opts = default_opts()
+    err = ctypes.create_string_buffer(256)
+    d = Dims(*dims)
+    st = lib.amm_solve_noalloc(batch, ctypes.byref(d), ctypes.byref(opts), _ptr(H), _ptr(alpha), _ptr(sigma2),
+                               _ptr(P), _ptr(V0), n_iters, _ptr(V_out), _ptr(wsr_out), _stream_handle(stream),
+                               err, len(err))
+    if st != AMM_OK:
+        raise AmmError(st, err.value.decode())
 
 
 DimsLike = Union[Tuple[int, int, int, int, int], Sequence[Tuple[int, int, int, int, int]]]

@@ -90,7 +90,7 @@ __host__ __device__ inline int lanczos_len(const InstDesc& D, int steps) {
 struct Layout {
   int m, n, Cn, CK, np, Lm;
   int ldh, ldv, ldz;
-  int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_w, off_tri, off_h;
+  int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_w, off_tri, off_h, off_alpha;
   int off_H, off_V, off_Z, off_L;
   int total;
 };
@@ -119,6 +119,7 @@ __host__ __device__ inline Layout plan_layout(const InstDesc& D, int budget, int
   L.off_tri = off;  off += 2 * (L.Lm + 1) * 4;
   off = align_up(off, 16);
   L.off_h = off;    off += (L.Lm + 1) * 8;
+  L.off_alpha = off; off += L.CK * 4;
   off = align_up(off, 128);
   const int szH = D.C * L.m * L.ldh * 8;
   const int szV = 2 * D.C * D.Nt * L.ldv * 8;

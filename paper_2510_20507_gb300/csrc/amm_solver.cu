@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   __shared__ int s_fail;
   __shared__ int s_ctrl[8];
   __shared__ float s_bcast;
+  __shared__ double s_rhoprev;
 
   const int b = blockIdx.x;
   const InstDesc D = p.desc[b];
@@ -74,9 +75,19 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   float* tb = ta + (Ly.Lm + 1);
   float2* lh = reinterpret_cast<float2*>(smem + Ly.off_h);
 
-  const float* alpha_u = p.alpha + D.u_off;
-  const float* Pc = p.P + D.c_off;
-  float* gamma_c = p.gamma_c + D.c_off;
+  // per-instance scalars live in shared memory for the whole launch:
+  // cellf[0,16) gamma, [16,32) projection scale, [32,48) P_k, [48,64) gamma_c
+  float* const s_alpha = reinterpret_cast<float*>(smem + Ly.off_alpha);
+  const float* alpha_u = s_alpha;
+  float* gamma_cg = p.gamma_c + D.c_off;
+  for (int r = tid; r < Ly.CK; r += blockDim.x) s_alpha[r] = p.alpha[D.u_off + r];
+  for (int k = tid; k < C; k += blockDim.x) {
+    cellf[32 + k] = p.P[D.c_off + k];
+    cellf[48 + k] = gamma_cg[k];
+  }
+  if (tid == 0) s_rhoprev = scg->rho_prev;
+  const float* Pc = cellf + 32;
+  float* gamma_c = cellf + 48;
   float2* Vg = p.V + D.v_off;
   float2* Vpg = p.Vprev + D.v_off;
   const float2* Hg = p.H + D.h_off;
@@ -161,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     }
     // ---- stage test of Algorithm 3 and the stopping test (thread 0)
     if (tid == 0)
-      stage_logic(s_ctrl, rho, scg->rho_prev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
+      stage_logic(s_ctrl, rho, s_rhoprev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
     __syncthreads();
     if (s_ctrl[4]) break;
     const int stage = s_ctrl[1];
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     cur ^= 1;
     zc ^= 1;
     if (tid == 0) {
-      scg->rho_prev = rho;
+      s_rhoprev = rho;
       s_ctrl[3] = stage;
       s_ctrl[0] = t + 1;
       s_ctrl[5] += 1;
@@ -260,6 +271,8 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   }
   if (tid == 0) {
     scg->t = s_ctrl[0];
+    scg->rho_prev = s_rhoprev;
+    for (int k = 0; k < C; ++k) gamma_cg[k] = gamma_c[k];
     scg->stage = s_ctrl[1];
     scg->stage_iter = s_ctrl[2];
     scg->last_stage = s_ctrl[3];

@@ -27,7 +27,8 @@ namespace amm {
 // hi*mid + mid*hi + mid*mid + hi*lo + lo*hi, about FP32 accuracy).
 __host__ __device__ inline int tc_splits(int prec) { return prec == 3 ? 3 : (prec == 2 ? 2 : 1); }
 // With three terms the gradient GEMM reads H_real^T as the MN-major view of
-// the forward operand instead of keeping a K-major copy.
+// the forward operand instead of keeping a K-major copy: the same 8 x 16-byte
+// core matrices, with 8-row groups of the forward operand now its K direction.
 __host__ __device__ inline bool tc_mn_gradient(int prec) { return prec == 3; }
 
 struct TcLayout {
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   __shared__ int s_fail;
   __shared__ int s_ctrl[8];
   __shared__ float s_bcast;
+  __shared__ double s_rhoprev;
 
   const int b = blockIdx.x;
   const InstDesc D = p.desc[b];
@@ -130,9 +132,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   float2* Zs = reinterpret_cast<float2*>(smem + T.off_Zs);
   float2* QL = (T.off_L >= 0) ? reinterpret_cast<float2*>(smem + T.off_L) : p.Lws + D.l_off;
 
-  const float* alpha_u = p.alpha + D.u_off;
+  // per-instance scalars live in shared memory for the whole launch
+  float* const s_alpha = reinterpret_cast<float*>(smem + Ly.off_alpha);
+  const float* alpha_u = s_alpha;
+  float* gamma_cg = p.gamma_c + D.c_off;
+  for (int r = tid; r < Ly.CK; r += blockDim.x) s_alpha[r] = p.alpha[D.u_off + r];
+  if (tid == 0) {
+    cellf[48] = gamma_cg[0];
+    s_rhoprev = scg->rho_prev;
+  }
   const float Pc = p.P[D.c_off];
-  float* gamma_c = p.gamma_c + D.c_off;
+  float* gamma_c = cellf + 48;
   float2* Vg = p.V + D.v_off;
   float2* Vpg = p.Vprev + D.v_off;
   const float2* Hg = p.H + D.h_off;
@@ -239,13 +249,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     if (tid == 0) {
       tc::fence_after_sync();
       const uint32_t idesc = tc::idesc_bf16(128, Np) | (mn ? (1u << 15) : 0u);
+      // no swizzle: LBO is the stride between core matrices along K, SBO along M/N,
+      // for K-major and MN-major operands alike
       const unsigned sbo_b = (unsigned)(Kp / 8) * 128u;
-      const unsigned sbo_a = mn ? (unsigned)(T.K1p / 8) * 128u : sbo_b;
+      const unsigned lbo_a = mn ? (unsigned)(T.K1p / 8) * 128u : 128u;
+      const unsigned sbo_a = mn ? 128u : sbo_b;
       for (int kk = 0; kk < Kp / 16; ++kk) {
-        const unsigned aoff = mn ? (unsigned)kk * 2u * sbo_a : (unsigned)kk * 256u;
+        const unsigned aoff = mn ? (unsigned)kk * 2u * lbo_a : (unsigned)kk * 256u;
         const unsigned boff = (unsigned)kk * 256u;
         for (int q = 0; q < npairs; ++q) {
-          tc::mma_bf16(tbase + dcol, tc::smem_desc(tc::su32(Ar[pa[q]]) + aoff, 128u, sbo_a),
+          tc::mma_bf16(tbase + dcol, tc::smem_desc(tc::su32(Ar[pa[q]]) + aoff, lbo_a, sbo_a),
                        tc::smem_desc(tc::su32(Bs[pb[q]]) + boff, 128u, sbo_b), idesc, (kk > 0 || q > 0) ? 1u : 0u);
         }
       }
@@ -299,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true, red, &s_fail);
     if (s_fail != kOk) break;
     if (tid == 0)
-      stage_logic(s_ctrl, rho, scg->rho_prev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
+      stage_logic(s_ctrl, rho, s_rhoprev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
     __syncthreads();
     if (s_ctrl[4]) break;
     const int stage = s_ctrl[1];
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     zc ^= 1;
     write_B1(colV[cur]);
     if (tid == 0) {
-      scg->rho_prev = rho;
+      s_rhoprev = rho;
       s_ctrl[3] = stage;
       s_ctrl[0] = t + 1;
       s_ctrl[5] += 1;
@@ -434,6 +447,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   if (warp == 0) tc::tmem_dealloc(tbase, (unsigned)T.ncols);
   if (tid == 0) {
     scg->t = s_ctrl[0];
+    scg->rho_prev = s_rhoprev;
+    for (int k = 0; k < 1; ++k) gamma_cg[k] = gamma_c[k];
     scg->stage = s_ctrl[1];
     scg->stage_iter = s_ctrl[2];
     scg->last_stage = s_ctrl[3];

@@ -309,6 +309,41 @@ def run_gpu(args):
     elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     value = whole_job_rate(world, batch, args.steps, elapsed_ms / 1000.0)
 
+    # ---- the plain FP32 GEMM path on the same inputs, timed the same way
+    plain = None
+    if args.precision != "fp32" and not args.no_plain:
+        popts = pkg.default_opts(precision="fp32", fp64_solves=opts.fp64_solves)
+        psolver = pkg.Solver(batch, pk.dims[0], opts=popts, stream=stream)
+
+        def plain_step():
+            psolver.set_problem(H, alpha, sigma2, P)
+            psolver.warmstart(G0)
+            psolver.step(ITERS)
+            psolver.wsr(wsr)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                plain_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            p0.record(stream)
+            for _ in range(args.steps):
+                plain_step()
+            p1.record(stream)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(p0.elapsed_time(p1), dist, dev)
+        pval = whole_job_rate(world, batch, args.steps, pms / 1000.0)
+        plain = {"precision": "fp32", "value": pval, "unit": UNIT, "ms_per_step": pms / args.steps}
+        psolver.close()
+        # restore this step's result for the parity sample below
+        with torch.cuda.stream(stream):
+            one_step()
+        torch.cuda.synchronize()
+
     # ---- end to end through the C-ABI with host buffers (pinned)
     e2e_value, h2d, d2h = None, 0, 0
     if not args.no_e2e:
@@ -375,6 +410,8 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "iterate_kernel_ms": avg_iter_ms,
+        "plain_path": plain,
+        "speedup_vs_plain": (value / plain["value"]) if plain else None,
         "parity": parity,
     }
     if rank == 0:
@@ -391,11 +428,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default="bf16x6", choices=["fp32", "bf16", "bf16x3", "bf16x6"])
     ap.add_argument("--smem-budget", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 path alongside")
     ap.add_argument("--fp32-solves", action="store_true",
                     help="run the per-user Hermitian solves in FP32 instead of FP64")
     ap.add_argument("--instances", type=int, default=0,

@@ -5,7 +5,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -60,6 +62,7 @@ struct amm_ctx {
   cudaStream_t stream = nullptr;
   std::vector<InstDesc> hdesc;
   InstDesc* ddesc = nullptr;
+  int* dorder = nullptr;  // block -> instance, longest first (uneven batches only)
   long long h_elems = 0, v_elems = 0, n_users = 0, n_cells = 0, z_elems = 0, l_elems = 0;
   float2* H = nullptr;
   float* alpha = nullptr;
@@ -151,7 +154,7 @@ static cudaError_t dalloc(T** p, long long count) {
 }
 
 static void free_all(amm_ctx* c) {
-  void* ptrs[] = {c->ddesc, c->H,     c->alpha,    c->P,         c->V,    c->Vprev,  c->Zws,   c->Lws,
+  void* ptrs[] = {c->ddesc, c->dorder, c->H,     c->alpha,    c->P,         c->V,    c->Vprev,  c->Zws,   c->Lws,
                   c->sc,    c->gamma_c, c->Hin,   c->alpha_in, c->sigma2_in, c->P_in, c->V0_in, c->wsr_dev};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -248,6 +251,25 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
     return fail(nullptr, e == cudaErrorMemoryAllocation ? AMM_ENOMEM : AMM_ECUDA,
                 std::string("device allocation failed: ") + cudaGetErrorString(e));
   }
+  if (n_dims > 1) {
+    // longest processing time first: blocks are scheduled roughly in index
+    // order, so the costliest instances start first and the short ones fill in
+    std::vector<double> cost(batch);
+    for (int b = 0; b < batch; ++b) {
+      const InstDesc& D = c->hdesc[b];
+      const double m = (double)D.C * D.K * D.Nr, n = (double)D.K * D.d;
+      cost[b] = 2.0 * D.C * m * D.Nt * n + 400.0 * D.C * D.K;  // GEMMs + per-user solves
+    }
+    std::vector<int> ord(batch);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    if ((e = dalloc(&c->dorder, batch)) ||
+        (e = cudaMemcpy(c->dorder, ord.data(), sizeof(int) * batch, cudaMemcpyHostToDevice))) {
+      free_all(c);
+      delete c;
+      return fail(nullptr, AMM_ECUDA, std::string("set-up failed: ") + cudaGetErrorString(e));
+    }
+  }
   if ((e = cudaMemcpy(c->ddesc, c->hdesc.data(), sizeof(InstDesc) * batch, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(Scalars) * batch)) ||
       // the limit is per kernel, not per context: raise it to the largest budget any
@@ -305,6 +327,7 @@ static amm::IterParams base_params(amm_ctx* c) {
   amm::IterParams p;
   memset(&p, 0, sizeof p);
   p.desc = c->ddesc;
+  p.order = c->dorder;
   p.H = c->H;
   p.alpha = c->alpha;
   p.P = c->P;

@@ -45,6 +45,7 @@ struct Scalars {
 
 struct IterParams {
   const InstDesc* desc;
+  const int* order;    // block -> instance (longest first for uneven batches); null = identity
   const float2* H;     // channels scaled by 1/sigma per user
   const float* alpha;  // per user
   const float* P;      // per cell

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   __shared__ float s_bcast;
   __shared__ double s_rhoprev;
 
-  const int b = blockIdx.x;
+  const int b = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const InstDesc D = p.desc[b];
   Scalars* scg = p.sc + b;
   const int tid = threadIdx.x;

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   __shared__ float s_bcast;
   __shared__ double s_rhoprev;
 
-  const int b = blockIdx.x;
+  const int b = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const InstDesc D = p.desc[b];
   Scalars* scg = p.sc + b;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

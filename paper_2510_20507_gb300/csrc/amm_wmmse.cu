@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) wmmse_kernel(IterParams p, float bis
   __shared__ int s_fail;
   __shared__ float s_piv;
 
-  const int b = blockIdx.x;
+  const int b = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const InstDesc D = p.desc[b];
   Scalars* scg = p.sc + b;
   const int tid = threadIdx.x;

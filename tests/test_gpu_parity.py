@@ -345,3 +345,47 @@ def test_contexts_of_different_sizes_coexist():
     assert np.all(np.isfinite(a.wsr())) and np.all(np.isfinite(b.wsr()))
     a.close()
     b.close()
+
+
+def test_uneven_batch_sampled():
+    """An uneven batch (Nt in 16..256, K in 4..64, Nr in {1, 2, 4},
+    d = min(Nr, 2), P = 0..30 dB): one launch, blocks ordered longest first;
+    the largest instances keep H, V and Z in global memory.  Sampled
+    instances re-solved by the oracle."""
+    insts = wl.uneven(n=4096, count=192)
+    iters = 30
+    g = GpuRun(insts)
+    g.warmstart()
+    g.step(iters)
+    got = g.wsr()
+    assert np.all(g.status() == 0)
+    cost = [i.K * i.K * i.Nr * i.Nt * i.d for i in insts]
+    order = np.argsort(cost)
+    sample = list(order[:4]) + [order[len(order) // 2], order[-1]]
+    for b in sample:
+        ref = oracle_run(insts[b], iters)
+        if switch_margin(ref) < 1e-4:
+            continue
+        want = oracle_wsr_bits(insts[b], ref.V)
+        assert abs(got[b] - want) <= WSR_TOL * want, (b, insts[b].dims, got[b], want)
+    g.close()
+
+
+def test_seven_cell_layout_sampled():
+    """Seven hexagonal cells (Nt=128, K=10, Nr=2, d=2, path loss and
+    shadowing, -104 dBm noise, 46 dBm per BS): the multi-cell path, channels
+    normalised by the noise level inside amm_set_problem."""
+    insts = wl.hex7(n=256, count=24)
+    iters = 50
+    g = GpuRun(insts)
+    g.warmstart()
+    g.step(iters)
+    got = g.wsr()
+    assert np.all(g.status() == 0)
+    for b in (0, 17):
+        ref = oracle_run(insts[b], iters)
+        if switch_margin(ref) < 1e-4:
+            continue
+        want = oracle_wsr_bits(insts[b], ref.V)
+        assert abs(got[b] - want) <= WSR_TOL * want, (b, got[b], want)
+    g.close()

@@ -110,6 +110,22 @@ def oracle_wsr_bits(inst, V):
     return om.wsr_bits(inst.H, V, inst.sigma2, inst.alpha, inst.K, inst.Nr, inst.d)
 
 
+def oracle_rounding_spread(inst, iters):
+    """Relative change of the oracle's final WSR when only the N_r x N_r
+    receive covariance of eq. (9) is stored in FP32 (complex64) and all else
+    stays FP64: how much FP32-level rounding alone moves this instance's
+    trajectory.  Above about 1e-4 the instance's 50-iteration WSR is not
+    determined to 1e-3 by FP32 arithmetic."""
+    exact = om.receive_covariance
+    ref = oracle_wsr_bits(inst, oracle_run(inst, iters).V)
+    om.receive_covariance = lambda *a: exact(*a).astype(np.complex64).astype(np.complex128)
+    try:
+        rounded = oracle_wsr_bits(inst, oracle_run(inst, iters).V)
+    finally:
+        om.receive_covariance = exact
+    return abs(rounded - ref) / ref
+
+
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 

@@ -351,23 +351,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       put(Bs, c, k, T.K2p, z, false);
     }
     __syncthreads();
-    // ---- S5: step size, eq. (16); Lanczos reads H back from the split operand
+    // ---- S5: step size, eq. (16).  The Z staging buffer is idle now (Y has been
+    //      formed from it): when the FP32 channel fits there, Lanczos reads it
+    //      from shared memory; otherwise it sums the bf16 split terms.
     {
       const int sflag = s_ctrl[6];
       float gk;
       if (sflag & 1) {
-        const float lam = lanczos_norm(
-            D, Ly,
-            [&](int i, int q) {
-              float re = 0.f, im = 0.f;
-              for (int t = NS - 1; t >= 0; --t) {  // small terms first
-                re += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(i, q, T.K1p)));
-                im += __bfloat162float(
-                    *reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(m + i, q, T.K1p)));
-              }
-              return make_float2(re, im);
-            },
-            sU, sP, alpha_u, QL, ly, lz, lw, ta, tb, lh, red, &s_bcast);
+        float lam;
+        if (Nt <= ldz) {
+          for (int e = tid; e < m * Nt; e += blockDim.x) {
+            const int i = e / Nt, q = e - i * Nt;
+            Zs[(long long)i * ldz + q] = Hg[e];
+          }
+          __syncthreads();
+          lam = lanczos_norm(
+              D, Ly, [&](int i, int q) { return Zs[(long long)i * ldz + q]; }, sU, sP, alpha_u, QL, ly, lz, lw, ta,
+              tb, lh, red, &s_bcast);
+        } else {
+          lam = lanczos_norm(
+              D, Ly,
+              [&](int i, int q) {
+                float re = 0.f, im = 0.f;
+                for (int t = NS - 1; t >= 0; --t) {  // small terms first
+                  re += __bfloat162float(
+                      *reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(i, q, T.K1p)));
+                  im += __bfloat162float(
+                      *reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(m + i, q, T.K1p)));
+                }
+                return make_float2(re, im);
+              },
+              sU, sP, alpha_u, QL, ly, lz, lw, ta, tb, lh, red, &s_bcast);
+        }
         gk = (lam > 0.f) ? 1.f / lam : 0.f;
         if ((sflag & 2) && tid == 0) gamma_c[0] = gk;
       } else {

@@ -121,7 +121,7 @@ extern "C" void amm_default_opts(amm_opts* o) {
   o->step_rule = 0;
   o->precision = AMM_FP32;
   o->u_at_extrapolated = 0;
-  o->lanczos_steps = 20;
+  o->lanczos_steps = 32;
   o->spin_budget = 2000000000ll;  // SM clock cycles, about one second
   o->smem_budget = 0;
   o->fp64_solves = 1;

@@ -337,30 +337,42 @@ static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, b
 }
 
 // ------------------------------------------------------- Lanczos ||F_k||_2
-// Largest eigenvalue of the Lanczos tridiagonal T (diagonal a, off-diagonal
-// b) by multisection on the Sturm count, run by warp 0 (FP32).
-static __device__ __noinline__ float tridiag_max_eig(const float* a, const float* b, int n) {
-  const int lane = threadIdx.x & 31;
-  float lo = a[0], hi = a[0];
-  for (int i = 0; i < n; ++i) {
-    const float r = (i > 0 ? fabsf(b[i - 1]) : 0.f) + (i + 1 < n ? fabsf(b[i]) : 0.f);
-    lo = fmaxf(lo, a[i]);
-    hi = fmaxf(hi, a[i] + r);
-  }
-  const float scale = fmaxf(fabsf(hi), 1e-30f);
-  for (int round = 0; round < 8; ++round) {
-    const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
-    // number of eigenvalues below x (negative pivots of T - x I)
-    int below = 0;
-    float q = a[0] - x;
+// Number of eigenvalues of the symmetric tridiagonal T (diagonal a,
+// off-diagonal b, order n) below x: the negative pivots of T - x I (Sturm
+// count, FP32, tiny pivots pushed to the negative side).
+static __device__ __forceinline__ int sturm_below(const float* a, const float* b, int n, float x, float scale) {
+  int below = 0;
+  float q = a[0] - x;
+  if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
+  below += q < 0.f;
+  for (int i = 1; i < n; ++i) {
+    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
     if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
     below += q < 0.f;
-    for (int i = 1; i < n; ++i) {
-      q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
-      if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
-      below += q < 0.f;
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, below < n);  // some eigenvalue >= x
+  }
+  return below;
+}
+
+// Gershgorin upper bound of the spectrum of T.
+static __device__ __forceinline__ float tridiag_gershgorin(const float* a, const float* b, int n) {
+  float hi = a[0];
+  for (int i = 0; i < n; ++i) {
+    const float r = (i > 0 ? fabsf(b[i - 1]) : 0.f) + (i + 1 < n ? fabsf(b[i]) : 0.f);
+    hi = fmaxf(hi, a[i] + r);
+  }
+  return hi;
+}
+
+// Multisection on the Sturm count by warp 0, 32 points per round: narrows a
+// bracket [lo, hi] that holds the largest eigenvalue of T (order n) down to
+// FP32 resolution.  Returns the final bracket (x = lower end, y = upper end).
+static __device__ __noinline__ float2 tridiag_top_refine(const float* a, const float* b, int n, float lo, float hi) {
+  const int lane = threadIdx.x & 31;
+  if (hi < lo) hi = lo;
+  const float scale = fmaxf(fabsf(hi), 1e-30f);
+  for (int round = 0; round < 8 && hi - lo > 1.2e-7f * hi; ++round) {
+    const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+    const unsigned mask = __ballot_sync(0xffffffffu, sturm_below(a, b, n, x, scale) < n);  // some eigenvalue >= x
     if (mask == 0u) {
       hi = lo + (hi - lo) / 33.f;
     } else {
@@ -371,7 +383,45 @@ static __device__ __noinline__ float tridiag_max_eig(const float* a, const float
       hi = nhi;
     }
   }
-  return 0.5f * (lo + hi);
+  return make_float2(lo, hi);
+}
+
+// Relative tolerance on the largest Ritz value between two checks, and the
+// size of b_j, relative to the largest a_j, below which the Krylov space
+// counts as invariant (what remains of w is then FP32 rounding).
+constexpr float kLanczosTol = 1e-6f;
+constexpr float kLanczosBreak = 1e-5f;
+
+// Convergence check of the largest Ritz value, warp 0.  *lb holds a lower
+// bound of the largest eigenvalue of the previous check's T, accurate to FP32
+// resolution (0 before the first check).  By interlacing the largest Ritz
+// value never decreases with the step, so *lb bounds the current T's from
+// below too.  One Sturm round tests x_l = lb (1 + tol 2^l), l = 0..31: when
+// no eigenvalue reaches x_0 the value moved by less than tol since the last
+// check and the call returns true; otherwise the bracket between the
+// highest x_l reached and the next one is refined and *lb rises to it.
+static __device__ __noinline__ bool tridiag_top_settled(const float* a, const float* b, int n, float* lb) {
+  const int lane = threadIdx.x & 31;
+  const float base = *lb;
+  const float gh = tridiag_gershgorin(a, b, n);
+  if (!(base > 0.f)) {
+    float amax = a[0];
+    for (int i = 1; i < n; ++i) amax = fmaxf(amax, a[i]);
+    const float2 br = tridiag_top_refine(a, b, n, amax, gh);
+    if (lane == 0) *lb = br.x;
+    return false;
+  }
+  const float scale = fmaxf(fabsf(gh), 1e-30f);
+  const float x = base * (1.f + kLanczosTol * ldexpf(1.f, lane));
+  const unsigned mask = __ballot_sync(0xffffffffu, sturm_below(a, b, n, x, scale) < n);
+  if ((mask & 1u) == 0u) return true;
+  const int l = 31 - __clz(mask);
+  const float lo = base * (1.f + kLanczosTol * ldexpf(1.f, l));
+  const float hi = (l == 31) ? gh : base * (1.f + kLanczosTol * ldexpf(1.f, l + 1));
+  const float2 br = tridiag_top_refine(a, b, n, lo, hi);
+  __syncwarp();
+  if (lane == 0) *lb = br.x;
+  return false;
 }
 
 struct Views {
@@ -386,11 +436,16 @@ struct Views {
 
 // Lanczos on F_k x = Htilde_k^H D Htilde_k x, D = blkdiag(2 alpha U W U^H).
 // Each step forms w = F_k q_j and orthogonalises it against every previous
-// basis vector by one classical Gram-Schmidt pass on the raw vector, which
-// also yields the recurrence coefficient a_j = Re(q_j^H w); b_j = ||w||.
-// Returns lambda_max of the tridiagonal (exact once the Krylov space is
-// invariant; with FP32 and 20 steps within ~1e-7 of ||F_k||_2 on the
-// workloads here).  Contains __syncthreads(); FP32 reductions only.
+// basis vector by two classical Gram-Schmidt passes (the second restores
+// orthogonality to FP32 precision; one pass loses it over a few dozen steps
+// and then the tridiagonal's eigenvalues leave F_k's spectrum).  The passes'
+// coefficients of q_j sum to a_j; b_j = ||w||.  From step 8 on, every second
+// step tests whether the largest Ritz value still moves by more than
+// kLanczosTol (tridiag_top_settled); the iteration ends there, at an
+// invariant Krylov space (b_j below kLanczosBreak times the largest a_j) or
+// at Ly.Lm steps.  Returns the largest
+// Ritz value, an estimate of lambda_max(F_k) from below.  Contains
+// __syncthreads(); FP32 reductions only.
 template <class HGet>
 __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, const float2* sU, const float2* sP,
                               const float* alpha_u, float2* QL, float2* y, float2* z, float2* w, float* ta, float* tb,
@@ -398,6 +453,8 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
   const int Nt = D.Nt, m = Ly.m, Nr = D.Nr, d = D.d;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   float* redf = reinterpret_cast<float*>(red);
+  float* s_lb = redf + 32;   // lower bound of the largest Ritz value (warp 0)
+  float* s_done = redf + 33; // settled flag, read by every thread after a barrier
   // group of g threads per output row, g a power of two <= 32
   int g = 1;
   while (g < 32 && 2 * g * m <= (int)blockDim.x) g <<= 1;
@@ -410,9 +467,15 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
     sincosf(6.2831853f * 0.6180339887f * (float)(p + 1), &s, &c);
     QL[p] = make_float2(c * rn, s * rn);
   }
+  if (tid == 0) {
+    *s_lb = 0.f;
+    *s_done = 0.f;
+  }
   __syncthreads();
   const int Lm = Ly.Lm;
   int Leff = Lm;
+  bool settled = false;
+  float amax = 0.f;  // largest a_j so far (a lower bound of lambda_max)
   for (int j = 0; j < Lm; ++j) {
     const float2* q = QL + (long long)j * Nt;
     // y = Htilde_k q
@@ -459,46 +522,69 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
       if (act && l == 0) w[p] = acc;
     }
     __syncthreads();
-    // h_i = q_i^H w, i <= j (one warp per i)
-    for (int i = warp; i <= j; i += nw) {
-      const float2* qi = QL + (long long)i * Nt;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int p = lane; p < Nt; p += 32) acc = cjfma(qi[p], w[p], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) h[i] = acc;
+    // two passes of w <- w - sum_i (q_i^H w) q_i, i <= j; ||w||^2 after the second
+    float aj = 0.f, ss = 0.f;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = warp; i <= j; i += nw) {  // h_i = q_i^H w, one warp per i
+        const float2* qi = QL + (long long)i * Nt;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int p = lane; p < Nt; p += 32) acc = cjfma(qi[p], w[p], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) h[i] = acc;
+      }
+      __syncthreads();
+      aj += h[j].x;
+      float nn = 0.f;
+      for (int p = tid; p < Nt; p += blockDim.x) {
+        float2 v = w[p];
+        for (int i = 0; i <= j; ++i) v = csub(v, cmul(h[i], QL[(long long)i * Nt + p]));
+        w[p] = v;
+        nn += cabs2(v);
+      }
+      if (pass == 1) {
+        nn = warp_sum(nn);
+        if (lane == 0) redf[warp] = nn;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // w <- w - sum_i h_i q_i, and ||w||^2
-    float nn = 0.f;
-    for (int p = tid; p < Nt; p += blockDim.x) {
-      float2 v = w[p];
-      for (int i = 0; i <= j; ++i) v = csub(v, cmul(h[i], QL[(long long)i * Nt + p]));
-      w[p] = v;
-      nn += cabs2(v);
-    }
-    nn = warp_sum(nn);
-    if (lane == 0) redf[warp] = nn;
-    __syncthreads();
-    float ss = 0.f;
     for (int q2 = 0; q2 < nw; ++q2) ss += redf[q2];  // same order in every thread
     const float bj = sqrtf(ss);
-    const float aj = h[j].x;
     if (tid == 0) {
       ta[j] = aj;
       tb[j] = bj;
     }
-    if (j + 1 >= Lm || !(bj > 1e-6f * fabsf(aj))) {
+    amax = fmaxf(amax, aj);
+    // an invariant Krylov space: what is left of w is rounding noise
+    if (j + 1 >= Lm || !(bj > kLanczosBreak * amax)) {
       Leff = j + 1;
       break;
     }
     const float ib = 1.f / bj;
     float2* qn = QL + (long long)(j + 1) * Nt;
     for (int p = tid; p < Nt; p += blockDim.x) qn[p] = cscale(w[p], ib);
+    if (warp == 0 && j + 1 >= 8 && ((j + 1) & 1) == 0) {
+      __syncwarp();  // ta[j] from lane 0
+      const bool done = tridiag_top_settled(ta, tb, j + 1, s_lb);
+      if (lane == 0 && done) *s_done = 1.f;
+    }
     __syncthreads();
+    if (*s_done != 0.f) {
+      Leff = j + 1;
+      settled = true;
+      break;
+    }
   }
   __syncthreads();
   if (tid < 32) {
-    const float lam = tridiag_max_eig(ta, tb, Leff);
+    float lam;
+    if (settled) {
+      lam = *s_lb * (1.f + 0.5f * kLanczosTol);
+    } else {
+      float lo = fmaxf(*s_lb, ta[0]);
+      for (int i = 1; i < Leff; ++i) lo = fmaxf(lo, ta[i]);
+      const float2 br = tridiag_top_refine(ta, tb, Leff, lo, tridiag_gershgorin(ta, tb, Leff));
+      lam = 0.5f * (br.x + br.y);
+    }
     if (tid == 0) *bcast = lam;
   }
   __syncthreads();

@@ -73,14 +73,13 @@ __host__ __device__ inline int pad_ld(int x) {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Krylov steps for ||F_k||_2.  F_k has rank <= C*K*d, so from a generic start
-// vector the Krylov space has dimension <= C*K*d + 1 (the start vector's
-// component in the null space adds one); with that many steps and full
-// reorthogonalisation the largest Ritz value is exact.
+// Largest number of Krylov steps for ||F_k||_2: the option's maximum, at most
+// Nt (the dimension of the space).  The iteration stops earlier once the
+// largest Ritz value has settled or the Krylov space has become invariant.
+// (In FP32 the space can take a step or two more than rank(F_k) + 1 to
+// become numerically invariant, so the rank is no cap.)
 __host__ __device__ inline int lanczos_len(const InstDesc& D, int steps) {
   int cap = D.Nt;
-  int rk = D.C * D.K * D.d + 1;
-  if (rk < cap) cap = rk;
   if (steps < cap) cap = steps;
   if (cap > kMaxLanczos) cap = kMaxLanczos;
   return cap < 1 ? 1 : cap;

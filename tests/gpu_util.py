@@ -110,20 +110,65 @@ def oracle_wsr_bits(inst, V):
     return om.wsr_bits(inst.H, V, inst.sigma2, inst.alpha, inst.K, inst.Nr, inst.d)
 
 
-def oracle_rounding_spread(inst, iters):
-    """Relative change of the oracle's final WSR when only the N_r x N_r
-    receive covariance of eq. (9) is stored in FP32 (complex64) and all else
-    stays FP64: how much FP32-level rounding alone moves this instance's
-    trajectory.  Above about 1e-4 the instance's 50-iteration WSR is not
-    determined to 1e-3 by FP32 arithmetic."""
-    exact = om.receive_covariance
-    ref = oracle_wsr_bits(inst, oracle_run(inst, iters).V)
-    om.receive_covariance = lambda *a: exact(*a).astype(np.complex64).astype(np.complex128)
+# An instance is FP32-sensitive when perturbations of the size of FP32
+# rounding move the oracle's own final WSR by more than this (relative).
+# Instances off the sensitive regime move by 1e-7 or less.
+SENSITIVE = 1e-5
+
+
+def _perturbed_wsr(inst, iters, cov32, v32, step_rel):
+    exact_cov, exact_step = om.receive_covariance, om.spectral_step
+    if cov32:
+        om.receive_covariance = lambda *a: exact_cov(*a).astype(np.complex64).astype(np.complex128)
+    if step_rel:
+        om.spectral_step = lambda *a: exact_step(*a) * (1 + step_rel)
     try:
-        rounded = oracle_wsr_bits(inst, oracle_run(inst, iters).V)
+        V0 = osv.initial_precoder(inst.G0, inst.P)
+        st = osv.AState(V=V0.copy(), Vprev=V0.copy())
+        for _ in range(iters):
+            osv.ammmse_iteration(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, st,
+                                 osv.Options())
+            if v32:
+                st.V = st.V.astype(np.complex64).astype(np.complex128)
+        return oracle_wsr_bits(inst, st.V)
     finally:
-        om.receive_covariance = exact
-    return abs(rounded - ref) / ref
+        om.receive_covariance, om.spectral_step = exact_cov, exact_step
+
+
+def oracle_fp32_spread(inst, iters):
+    """Largest relative change of the oracle's final WSR under FP32-sized
+    perturbations of its otherwise FP64 arithmetic: the N_r x N_r receive
+    covariance of eq. (9) stored in complex64, the iterate V stored in
+    complex64 after every iteration, the spectral step of eq. (16) off by
+    5e-7 relative (the accuracy of an FP32 Lanczos estimate of ||F_k||_2),
+    and all three together.  Single perturbations can cancel by chance on a
+    sensitive instance; the largest of the four is the estimate."""
+    ref = oracle_wsr_bits(inst, oracle_run(inst, iters).V)
+    variants = [(True, False, 0.0), (False, True, 0.0), (False, False, -5e-7), (True, True, 5e-7)]
+    return max(abs(_perturbed_wsr(inst, iters, *v) - ref) / ref for v in variants)
+
+
+def check_free_running(got, insts, iters, label, sample=None, tol=1e-3):
+    """Final WSR of a free-running GPU solve against the oracle, instance by
+    instance: within tol, unless the instance is FP32-sensitive (its
+    trajectory is then not fixed to tol by any FP32 arithmetic; such
+    instances are bounded by 5e-2 and reported).  Instances whose oracle
+    trajectory takes the stage decision within 1e-4 of eps1 are skipped.
+    Returns the list of (index, gap, spread) of sensitive instances beyond
+    tol."""
+    excused = []
+    for b in (range(len(insts)) if sample is None else sample):
+        ref = oracle_run(insts[b], iters)
+        if switch_margin(ref) < 1e-4:
+            continue
+        want = oracle_wsr_bits(insts[b], ref.V)
+        gap = abs(got[b] - want) / want
+        if gap > tol:
+            spread = oracle_fp32_spread(insts[b], iters)
+            print(f"{label}: instance {b} gap {gap:.2e}, oracle spread under FP32-sized perturbation {spread:.2e}")
+            assert spread > SENSITIVE and gap <= 5e-2, (label, b, got[b], want, spread)
+            excused.append((b, gap, spread))
+    return excused
 
 
 def rel(a, b):

@@ -12,10 +12,9 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import model as om
 from oracle import solvers as osv
 
-from gpu_util import GpuRun, oracle_rounding_spread, oracle_run, oracle_wsr_bits, rel, round_inputs, switch_margin, to_dev
+from gpu_util import GpuRun, check_free_running, oracle_run, oracle_wsr_bits, rel, round_inputs, switch_margin
 
 pytestmark = pytest.mark.gpu
 
@@ -128,12 +127,7 @@ def test_free_running(shape):
     g.warmstart()
     g.step(iters)
     got = g.wsr()
-    for b, inst in enumerate(insts):
-        ref = oracle_run(inst, iters)
-        if switch_margin(ref) < 1e-4:
-            continue
-        want = oracle_wsr_bits(inst, ref.V)
-        assert abs(got[b] - want) <= WSR_TOL * want, (shape, b, got[b], want)
+    check_free_running(got, insts, iters, f"free-running {shape}")
     g.close()
 
 
@@ -145,17 +139,11 @@ def test_tiny_fp64_workload_free_running():
     g.step(50)
     got = g.wsr()
     Vs = g.V()
-    gaps, verr = [], []
-    for b, inst in enumerate(insts):
-        ref = oracle_run(inst, 50)
-        if switch_margin(ref) < 1e-4:
-            continue
-        want = oracle_wsr_bits(inst, ref.V)
-        gaps.append(abs(got[b] - want) / want)
-        verr.append(rel(Vs[b], ref.V))
-    assert max(gaps) <= WSR_TOL, max(gaps)
-    print(f"tiny: max WSR gap {max(gaps):.2e}, median V err {np.median(verr):.2e}")
     g.close()
+    excused = check_free_running(got, insts, 50, "tiny")
+    assert len(excused) <= 2
+    verr = [rel(Vs[b], oracle_run(insts[b], 50).V) for b in range(0, 100, 10)]
+    print(f"tiny: median V err {np.median(verr):.2e}")
 
 
 @pytest.mark.parametrize("opt", [dict(step_rule=1), dict(extrapolate=0), dict(switch_iter=1),
@@ -191,13 +179,7 @@ def test_single_cell_64_full_batch_sampled():
     got = g.wsr()
     assert np.all(g.status() == 0)
     assert np.all(np.isfinite(got))
-    sample = [0, 1500, 2100, 3333, 4200, 5000, 6000, 7167]
-    for b in sample:
-        ref = oracle_run(insts[b], 50)
-        if switch_margin(ref) < 1e-4:
-            continue
-        want = oracle_wsr_bits(insts[b], ref.V)
-        assert abs(got[b] - want) <= WSR_TOL * want, (b, got[b], want)
+    check_free_running(got, insts, 50, "full batch", sample=[0, 1500, 2100, 3333, 4200, 5000, 6000, 7167])
     g.close()
 
 
@@ -347,11 +329,12 @@ def test_contexts_of_different_sizes_coexist():
     b.close()
 
 
-def _teacher_forced_errors(insts, iters, picks, **opts):
+def _teacher_forced_errors(insts, iters, picks, gpu_opts=None, **opts):
     """Worst relative V^t error of one GPU iteration started from the
-    oracle's state, over iterations 1..iters of the given instances."""
-    runs = {b: _oracle_states(insts[b], iters, osv.Options()) for b in picks}
-    g = GpuRun(insts, **opts)
+    oracle's state, over iterations 1..iters of the given instances (opts:
+    options both sides take under the same name; gpu_opts: GPU only)."""
+    runs = {b: _oracle_states(insts[b], iters, osv.Options(**opts)) for b in picks}
+    g = GpuRun(insts, **opts, **(gpu_opts or {}))
     worst = 0.0
     for t in range(iters):
         states = []
@@ -400,26 +383,13 @@ def test_seven_cell_layout_per_step():
 
 
 def _free_running_sampled(insts, iters, sample, label):
-    """Free-running solve of the whole batch; each sampled instance ends
-    within 1e-3 of the oracle's WSR, unless FP32 rounding of the receive
-    covariance alone moves the oracle's own result by more than 1e-4 there
-    (its trajectory is then not determined to 1e-3 by FP32 arithmetic)."""
     g = GpuRun(insts)
     g.warmstart()
     g.step(iters)
     got = g.wsr()
     assert np.all(g.status() == 0)
     g.close()
-    for b in sample:
-        ref = oracle_run(insts[b], iters)
-        if switch_margin(ref) < 1e-4:
-            continue
-        want = oracle_wsr_bits(insts[b], ref.V)
-        gap = abs(got[b] - want) / want
-        if gap > WSR_TOL:
-            spread = oracle_rounding_spread(insts[b], iters)
-            print(f"{label}: instance {b} gap {gap:.2e}, oracle spread under FP32 covariance {spread:.2e}")
-            assert spread > 1e-4, (label, b, got[b], want)
+    check_free_running(got, insts, iters, label, sample=sample)
 
 
 def test_uneven_batch_free_running():
@@ -432,3 +402,29 @@ def test_uneven_batch_free_running():
 
 def test_seven_cell_free_running():
     _free_running_sampled(round_inputs(wl.hex7(n=256, count=24)), 50, [0, 17], "seven cells")
+
+
+@pytest.mark.parametrize("shape", [(1, 48, 16, 2, 2), (1, 8, 256, 1, 1), (1, 35, 256, 1, 1), (1, 64, 256, 2, 2),
+                                   (1, 4, 64, 1, 1), (1, 16, 64, 4, 4), (2, 3, 17, 3, 2)])
+def test_spectral_step_every_iteration(shape):
+    """step_rule 1 takes gamma = 1/||F_k||_2 in every iteration, so every
+    step checks the Lanczos estimate of the largest eigenvalue of F_k:
+    shapes where the Krylov space fills all of C^Nt (Nt = 16), where
+    rank(F_k) is far below Nt, and where the top of the spectrum is dense
+    (K d = 128 of Nt = 256)."""
+    insts = small_batch(shape, 3, 7000 + sum(shape))
+    worst = _teacher_forced_errors(insts, 8, [0, 1, 2], step_rule=1)
+    print(f"spectral every iteration {shape}: teacher-forced worst rel err {worst:.2e}")
+    assert worst <= STEP_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
+def test_timed_workload_high_snr_per_step(prec):
+    """All 50 iterations of timed-workload instances at 0, 25 and 30 dB,
+    each started from the oracle's state: the per-step bound holds on the
+    instances whose free-running trajectories are FP32-sensitive too."""
+    picks = [100, 5488, 5570, 6495, 6992]
+    sub = round_inputs([wl.single_cell_64(first=b, count=1)[0] for b in picks])
+    worst = _teacher_forced_errors(sub, 50, list(range(len(sub))), gpu_opts=dict(precision=prec))
+    print(f"timed workload {prec}: teacher-forced worst rel err over 50 iterations {worst:.2e}")
+    assert worst <= STEP_TOL

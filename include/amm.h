@@ -93,10 +93,10 @@ typedef struct {
                            2: gamma_c every iteration (needs gamma_c > 0) */
   int precision;        /* amm_precision */
   int u_at_extrapolated;/* 0: U^t at V^{t-1};  1: U^t at the extrapolated point */
-  int lanczos_steps;    /* most Krylov steps for ||F_k||_2 (capped at Nt); the
-                           Lanczos iteration stops earlier once its largest
-                           Ritz value moves by less than 1e-6 relative over two
-                           steps; 32 */
+  int lanczos_steps;    /* most Lanczos steps for ||F_k||_2 (capped at Nt and 64);
+                           the iteration stops earlier once its largest Ritz
+                           value moves by less than 1e-6 relative over two
+                           steps; 64 */
   long long spin_budget;/* SM clock cycles any device-side wait may spin before
                            the instance gets AMM_ETIMEOUT; 2e9 (about 1 s) */
   int smem_budget;      /* bytes of shared memory per block the solver may use;
@@ -110,7 +110,7 @@ typedef struct amm_ctx amm_ctx;
 
 /* Fill *opts with the defaults: eps1 0.1, eps2 1e-3, tc 3, gamma_c 0,
  * extrapolate 1, switch_iter -1, step_rule 0, AMM_FP32, u_at_extrapolated 0,
- * lanczos_steps 32, spin_budget 2e9, smem_budget 0, fp64_solves 1. */
+ * lanczos_steps 64, spin_budget 2e9, smem_budget 0, fp64_solves 1. */
 AMM_API void amm_default_opts(amm_opts* opts);
 
 /* Create a solver for `batch` instances.  `dims` points to `n_dims` entries:

@@ -121,7 +121,7 @@ extern "C" void amm_default_opts(amm_opts* o) {
   o->step_rule = 0;
   o->precision = AMM_FP32;
   o->u_at_extrapolated = 0;
-  o->lanczos_steps = 32;
+  o->lanczos_steps = 64;
   o->spin_budget = 2000000000ll;  // SM clock cycles, about one second
   o->smem_budget = 0;
   o->fp64_solves = 1;
@@ -209,7 +209,7 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
     cc += D.C;
     const amm::Layout Lq = amm::plan_layout(D, amm::kSmemMax, o.lanczos_steps);
     z += 2 * m * Lq.ldz;
-    l += (long long)(Lq.Lm + 1) * D.Nt;
+    l += amm::lanczos_elems(D);
   }
   c->C = C0;
   c->h_elems = h; c->v_elems = v; c->n_users = u; c->n_cells = cc; c->z_elems = z; c->l_elems = l;

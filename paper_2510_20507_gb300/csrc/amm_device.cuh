@@ -434,38 +434,48 @@ struct Views {
   float2* QL;       // Krylov basis (Lm+1) x Nt
 };
 
-// Lanczos on F_k x = Htilde_k^H D Htilde_k x, D = blkdiag(2 alpha U W U^H).
-// Each step forms w = F_k q_j and orthogonalises it against every previous
-// basis vector by two classical Gram-Schmidt passes (the second restores
-// orthogonality to FP32 precision; one pass loses it over a few dozen steps
-// and then the tridiagonal's eigenvalues leave F_k's spectrum).  The passes'
-// coefficients of q_j sum to a_j; b_j = ||w||.  From step 8 on, every second
-// step tests whether the largest Ritz value still moves by more than
-// kLanczosTol (tridiag_top_settled); the iteration ends there, at an
-// invariant Krylov space (b_j below kLanczosBreak times the largest a_j) or
-// at Ly.Lm steps.  Returns the largest
-// Ritz value, an estimate of lambda_max(F_k) from below.  Contains
-// __syncthreads(); FP32 reductions only.
+// Lanczos on F_k x = Htilde_k^H D Htilde_k x, D = blkdiag(2 alpha U W U^H),
+// by the plain three-term recurrence
+//   w = F_k q_j - a_j q_j - b_{j-1} q_{j-1},  a_j = q_j^H F_k q_j,  b_j = ||w||,
+// without reorthogonalisation.  In floating point the basis loses
+// orthogonality as Ritz values converge, but every Ritz value stays within
+// the spectrum up to rounding (Paige's analysis of the finite-precision
+// recurrence), so the largest one converges to ||F_k||_2 from below; the
+// lost orthogonality only adds copies of converged values.  From step 8 on,
+// every second step tests whether the largest Ritz value still moves by
+// more than kLanczosTol (tridiag_top_settled); the iteration ends there, at
+// an invariant Krylov space (b_j below kLanczosBreak times the largest a_j)
+// or at Ly.Lm steps.
+//
+// Three barriers per step.  a_j = (Htilde q_j)^H D (Htilde q_j) is summed
+// while z = D y is formed; w is formed, updated and its norm taken by the
+// thread that owns its entry; q_{j+1} stays unnormalised in the slot of
+// q_{j-1} and its scale 1/b_j is applied where it is read.  QL holds the two
+// slots (2 Nt).  Contains __syncthreads(); FP32 reductions only.
 template <class HGet>
 __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, const float2* sU, const float2* sP,
-                              const float* alpha_u, float2* QL, float2* y, float2* z, float2* w, float* ta, float* tb,
-                              float2* h, double* red, float* bcast) {
+                              const float* alpha_u, float2* QL, float2* y, float2* z, float* ta, float* tb, double* red,
+                              float* bcast) {
   const int Nt = D.Nt, m = Ly.m, Nr = D.Nr, d = D.d;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   float* redf = reinterpret_cast<float*>(red);
-  float* s_lb = redf + 32;   // lower bound of the largest Ritz value (warp 0)
-  float* s_done = redf + 33; // settled flag, read by every thread after a barrier
+  float* s_apart = redf;        // [nw] partial sums of a_j
+  float* s_bpart = redf + 8;    // [nw] partial sums of b_j^2
+  float* s_lb = redf + 32;      // lower bound of the largest Ritz value (warp 0)
+  float* s_done = redf + 33;    // settled flag, read by every thread after a barrier
   // group of g threads per output row, g a power of two <= 32
   int g = 1;
   while (g < 32 && 2 * g * m <= (int)blockDim.x) g <<= 1;
   int gN = 1;
   while (gN < 32 && 2 * gN * Nt <= (int)blockDim.x) gN <<= 1;
-  // fixed start vector: unit-modulus entries with golden-ratio phases
+  float2* slot[2] = {QL, QL + Nt};
+  // fixed start vector: unit-modulus entries with golden-ratio phases; q_{-1} = 0
   const float rn = rsqrtf((float)Nt);
   for (int p = tid; p < Nt; p += blockDim.x) {
     float s, c;
     sincosf(6.2831853f * 0.6180339887f * (float)(p + 1), &s, &c);
-    QL[p] = make_float2(c * rn, s * rn);
+    slot[0][p] = make_float2(c * rn, s * rn);
+    slot[1][p] = make_float2(0.f, 0.f);
   }
   if (tid == 0) {
     *s_lb = 0.f;
@@ -475,25 +485,33 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
   const int Lm = Ly.Lm;
   int Leff = Lm;
   bool settled = false;
-  float amax = 0.f;  // largest a_j so far (a lower bound of lambda_max)
+  float amax = 0.f;                // largest a_j so far (a lower bound of lambda_max)
+  float sc_cur = 1.f, sc_prev = 0.f;  // q_j = sc_cur * slot[cur], q_{j-1} = sc_prev * slot[cur ^ 1]
+  float bprev = 0.f;
+  int cur = 0;
   for (int j = 0; j < Lm; ++j) {
-    const float2* q = QL + (long long)j * Nt;
-    // y = Htilde_k q
+    const float2* qj = slot[cur];
+    // y = Htilde_k q_j
     for (int e0 = 0; e0 < m * g; e0 += blockDim.x) {  // warp-uniform trip count for the shuffles
       const int e = e0 + tid;
       const bool act = e < m * g;
       const int i = act ? e / g : 0, l = e % g;
       float2 acc = make_float2(0.f, 0.f);
       if (act)
-        for (int p = l; p < Nt; p += g) acc = cfma(hget(i, p), q[p], acc);
+        for (int p = l; p < Nt; p += g) acc = cfma(hget(i, p), qj[p], acc);
       for (int o = g >> 1; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, g);
         acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, g);
       }
-      if (act && l == 0) y[i] = acc;
+      if (act && l == 0) y[i] = cscale(acc, sc_cur);
     }
     __syncthreads();
-    // z_r = 2 alpha_r P_r (U_r^H y_r)
+    if (*s_done != 0.f) {  // set by the previous step's check
+      settled = true;
+      break;
+    }
+    // z_r = 2 alpha_r P_r (U_r^H y_r), and a_j = sum_i Re(conj(y_i) z_i)
+    float apart = 0.f;
     for (int i = tid; i < m; i += blockDim.x) {
       const int r = i / Nr, a = i - r * Nr;
       const float2* Ur = sU + r * Nr * d;
@@ -504,10 +522,19 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
         for (int b = 0; b < Nr; ++b) ts = cjfma(Ur[b * d + s], y[r * Nr + b], ts);
         acc = cfma(Pr[a * d + s], ts, acc);
       }
-      z[i] = cscale(acc, 2.f * alpha_u[r]);
+      const float2 zi = cscale(acc, 2.f * alpha_u[r]);
+      z[i] = zi;
+      const float2 yi = y[i];
+      apart = fmaf(yi.x, zi.x, fmaf(yi.y, zi.y, apart));
     }
+    apart = warp_sum(apart);
+    if (lane == 0) s_apart[warp] = apart;
     __syncthreads();
-    // w = Htilde_k^H z
+    float aj = 0.f;
+    for (int q2 = 0; q2 < nw; ++q2) aj += s_apart[q2];  // same order in every thread
+    // w = Htilde_k^H z - a_j q_j - b_{j-1} q_{j-1}, into the slot of q_{j-1}
+    float2* qn = slot[cur ^ 1];
+    float bpart = 0.f;
     for (int e0 = 0; e0 < Nt * gN; e0 += blockDim.x) {
       const int e = e0 + tid;
       const bool act = e < Nt * gN;
@@ -519,35 +546,17 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, gN);
         acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, gN);
       }
-      if (act && l == 0) w[p] = acc;
+      if (act && l == 0) {
+        const float2 v = csub(csub(acc, cscale(qj[p], aj * sc_cur)), cscale(qn[p], bprev * sc_prev));
+        qn[p] = v;
+        bpart += cabs2(v);
+      }
     }
+    bpart = warp_sum(bpart);
+    if (lane == 0) s_bpart[warp] = bpart;
     __syncthreads();
-    // two passes of w <- w - sum_i (q_i^H w) q_i, i <= j; ||w||^2 after the second
-    float aj = 0.f, ss = 0.f;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int i = warp; i <= j; i += nw) {  // h_i = q_i^H w, one warp per i
-        const float2* qi = QL + (long long)i * Nt;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int p = lane; p < Nt; p += 32) acc = cjfma(qi[p], w[p], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) h[i] = acc;
-      }
-      __syncthreads();
-      aj += h[j].x;
-      float nn = 0.f;
-      for (int p = tid; p < Nt; p += blockDim.x) {
-        float2 v = w[p];
-        for (int i = 0; i <= j; ++i) v = csub(v, cmul(h[i], QL[(long long)i * Nt + p]));
-        w[p] = v;
-        nn += cabs2(v);
-      }
-      if (pass == 1) {
-        nn = warp_sum(nn);
-        if (lane == 0) redf[warp] = nn;
-      }
-      __syncthreads();
-    }
-    for (int q2 = 0; q2 < nw; ++q2) ss += redf[q2];  // same order in every thread
+    float ss = 0.f;
+    for (int q2 = 0; q2 < nw; ++q2) ss += s_bpart[q2];
     const float bj = sqrtf(ss);
     if (tid == 0) {
       ta[j] = aj;
@@ -559,19 +568,15 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
       Leff = j + 1;
       break;
     }
-    const float ib = 1.f / bj;
-    float2* qn = QL + (long long)(j + 1) * Nt;
-    for (int p = tid; p < Nt; p += blockDim.x) qn[p] = cscale(w[p], ib);
+    sc_prev = sc_cur;
+    sc_cur = 1.f / bj;
+    bprev = bj;
+    cur ^= 1;
+    // convergence check on T_{j+1}; the verdict is read after the next barrier
     if (warp == 0 && j + 1 >= 8 && ((j + 1) & 1) == 0) {
-      __syncwarp();  // ta[j] from lane 0
+      __syncwarp();  // ta[j], tb[j] from lane 0
       const bool done = tridiag_top_settled(ta, tb, j + 1, s_lb);
       if (lane == 0 && done) *s_done = 1.f;
-    }
-    __syncthreads();
-    if (*s_done != 0.f) {
-      Leff = j + 1;
-      settled = true;
-      break;
     }
   }
   __syncthreads();
@@ -623,11 +628,19 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
                                               const float2* sQ, float2* sU, float2* sUW, double* sRho,
                                               const float* alpha_u, bool want_u, double* red, int* fail) {
   const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, np = Ly.np, CK = Ly.CK;
-  // four lanes per user; the trip count is warp-uniform (the solve shuffles)
-  for (int base = 0; base < 4 * CK; base += blockDim.x) {
-    const int e = base + threadIdx.x;
-    const bool act = e < 4 * CK;
-    const int r = act ? e >> 2 : 0, c = e & 3;
+  // Four lanes per user.  The FP64 units are per SM sub-partition and a
+  // warp instruction costs the same however few lanes are active, so the
+  // users are spread over the first four warps (one per sub-partition)
+  // before any warp takes more: upw users per warp.  The trip count is
+  // warp-uniform (the solve shuffles).
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int upw = (CK + 3) >> 2;
+  if (upw > 8) upw = 8;
+  for (int base = 0; base < CK; base += nw * upw) {
+    const int u = lane >> 2, c = lane & 3;
+    const int rr = base + warp * upw + u;
+    const bool act = u < upw && rr < CK;
+    const int r = act ? rr : 0;
     if (!__any_sync(0xffffffffu, act)) continue;  // warps without a user skip the (FP64) solve
     const int own0 = (r / K) * n + (r % K) * d;
     double ld = 0.0;

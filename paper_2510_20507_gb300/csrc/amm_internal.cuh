@@ -85,12 +85,15 @@ __host__ __device__ inline int lanczos_len(const InstDesc& D, int steps) {
   return cap < 1 ? 1 : cap;
 }
 
+// Complex elements of the Lanczos vector storage: two slots of Nt.
+__host__ __device__ inline int lanczos_elems(const InstDesc& D) { return 2 * D.Nt; }
+
 // Byte offsets of the shared-memory regions of one instance.  Buffers that
 // do not fit the budget live in global memory (offset -1).
 struct Layout {
   int m, n, Cn, CK, np, Lm;
   int ldh, ldv, ldz;
-  int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_w, off_tri, off_h, off_alpha;
+  int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_tri, off_alpha;
   int off_H, off_V, off_Z, off_L;
   int total;
 };
@@ -115,16 +118,14 @@ __host__ __device__ inline Layout plan_layout(const InstDesc& D, int budget, int
   L.off_rho = off;  off += L.CK * 8;
   L.off_y = off;    off += L.m * 8;
   L.off_z = off;    off += L.m * 8;
-  L.off_w = off;    off += D.Nt * 8;
   L.off_tri = off;  off += 2 * (L.Lm + 1) * 4;
   off = align_up(off, 16);
-  L.off_h = off;    off += (L.Lm + 1) * 8;
   L.off_alpha = off; off += L.CK * 4;
   off = align_up(off, 128);
   const int szH = D.C * L.m * L.ldh * 8;
   const int szV = 2 * D.C * D.Nt * L.ldv * 8;
   const int szZ = 2 * L.m * L.ldz * 8;
-  const int szL = (L.Lm + 1) * D.Nt * 8;
+  const int szL = lanczos_elems(D) * 8;
   L.off_H = L.off_V = L.off_Z = L.off_L = -1;
   if (off + szH <= budget) { L.off_H = off; off += szH; }
   if (off + szV <= budget) { L.off_V = off; off += szV; }

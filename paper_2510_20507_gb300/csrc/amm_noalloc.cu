@@ -121,7 +121,7 @@ extern "C" amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const a
   const long long hs = C * m * d.nt, vs = C * d.nt * n, us = C * d.users, cs = C;
   // workspaces that the kernel keeps in shared memory need no scratch
   const long long zs = (Ly.off_Z < 0) ? 2 * m * Ly.ldz : 0;
-  const long long ls = (Ly.off_L < 0) ? (long long)(Ly.Lm + 1) * d.nt : 0;
+  const long long ls = (Ly.off_L < 0) ? (long long)lanczos_elems(proto) : 0;
 
   // carve the scratch array
   size_t off = 0;

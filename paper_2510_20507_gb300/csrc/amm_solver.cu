@@ -70,10 +70,8 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   double* sRho = reinterpret_cast<double*>(smem + Ly.off_rho);
   float2* ly = reinterpret_cast<float2*>(smem + Ly.off_y);
   float2* lz = reinterpret_cast<float2*>(smem + Ly.off_z);
-  float2* lw = reinterpret_cast<float2*>(smem + Ly.off_w);
   float* ta = reinterpret_cast<float*>(smem + Ly.off_tri);
   float* tb = ta + (Ly.Lm + 1);
-  float2* lh = reinterpret_cast<float2*>(smem + Ly.off_h);
 
   // per-instance scalars live in shared memory for the whole launch:
   // cellf[0,16) gamma, [16,32) projection scale, [32,48) P_k, [48,64) gamma_c
@@ -196,8 +194,8 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
       if (sflag & 1) {
         const float2* Hk = vw.H + (long long)k * m * ldh;
         const float lam = lanczos_norm(
-            D, Ly, [&](int i, int q) { return Hk[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, lw, ta,
-            tb, lh, red, &s_bcast);
+            D, Ly, [&](int i, int q) { return Hk[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, ta, tb,
+            red, &s_bcast);
         gk = (lam > 0.f) ? 1.f / lam : 0.f;
         if ((sflag & 2) && tid == 0) gamma_c[k] = gk;
       } else {

@@ -70,7 +70,7 @@ __host__ __device__ inline TcLayout plan_tc(const InstDesc& D, int budget, int l
   T.end_ops = off;
   T.off_Zs = off;  off += m * T.base.ldz * 8;
   off = align_up(off, 16);
-  const int szL = (T.base.Lm + 1) * D.Nt * 8;
+  const int szL = lanczos_elems(D) * 8;
   T.off_L = -1;
   if (off + szL <= budget) { T.off_L = off; off += szL; }
   T.total = off;
@@ -122,10 +122,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   double* sRho = reinterpret_cast<double*>(smem + Ly.off_rho);
   float2* ly = reinterpret_cast<float2*>(smem + Ly.off_y);
   float2* lz = reinterpret_cast<float2*>(smem + Ly.off_z);
-  float2* lw = reinterpret_cast<float2*>(smem + Ly.off_w);
   float* ta = reinterpret_cast<float*>(smem + Ly.off_tri);
   float* tb = ta + (Ly.Lm + 1);
-  float2* lh = reinterpret_cast<float2*>(smem + Ly.off_h);
   unsigned char* A1[3] = {smem + T.off_A1[0], smem + T.off_A1[1], smem + T.off_A1[2]};
   unsigned char* A2[3] = {smem + T.off_A2[0], smem + T.off_A2[1], smem + T.off_A2[2]};
   unsigned char* Bs[3] = {smem + T.off_B[0], smem + T.off_B[1], smem + T.off_B[2]};
@@ -366,8 +364,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
           }
           __syncthreads();
           lam = lanczos_norm(
-              D, Ly, [&](int i, int q) { return Zs[(long long)i * ldz + q]; }, sU, sP, alpha_u, QL, ly, lz, lw, ta,
-              tb, lh, red, &s_bcast);
+              D, Ly, [&](int i, int q) { return Zs[(long long)i * ldz + q]; }, sU, sP, alpha_u, QL, ly, lz, ta, tb,
+              red, &s_bcast);
         } else {
           lam = lanczos_norm(
               D, Ly,
@@ -381,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
                 }
                 return make_float2(re, im);
               },
-              sU, sP, alpha_u, QL, ly, lz, lw, ta, tb, lh, red, &s_bcast);
+              sU, sP, alpha_u, QL, ly, lz, ta, tb, red, &s_bcast);
         }
         gk = (lam > 0.f) ? 1.f / lam : 0.f;
         if ((sflag & 2) && tid == 0) gamma_c[0] = gk;

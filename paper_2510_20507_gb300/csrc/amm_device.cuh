@@ -189,7 +189,7 @@ __device__ __forceinline__ Cx<T> shfl4(Cx<T> v, int src) {
 // lanes without a user.  Returns false on a non-positive pivot.
 template <class T, int NR, int DD>
 __device__ bool small_solve_grp(int c, bool act, const float2* Qp, const float2* Zrow0, int ldz, int own0,
-                                float2* U, float2* UW, double* logdet, bool want_u) {
+                                float2* U, float2* UW, double* logdet, bool want_u, bool want_ld) {
   bool ok = act;
   Cx<T> L[NR][NR];
   T inv[NR];
@@ -278,7 +278,7 @@ __device__ bool small_solve_grp(int c, bool act, const float2* Qp, const float2*
     }
   }
   // log det(I + M): lane c contributes log1p of pivot c, summed over the group
-  double ld = (c < DD) ? (double)l1p(mypiv) : 0.0;
+  double ld = (want_ld && c < DD) ? (double)l1p(mypiv) : 0.0;
   ld += __shfl_xor_sync(0xffffffffu, ld, 1, 4);
   ld += __shfl_xor_sync(0xffffffffu, ld, 2, 4);
   if (c == 0) *logdet = ld;
@@ -325,9 +325,10 @@ __device__ bool small_solve_grp(int c, bool act, const float2* Qp, const float2*
 template <class T>
 static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, bool act, const float2* Qp,
                                                          const float2* Zrow0, int ldz, int own0, float2* U,
-                                                         float2* UW, double* logdet, bool want_u) {
+                                                         float2* UW, double* logdet, bool want_u, bool want_ld) {
 #define AMM_SS(a, b) \
-  if (Nr == a && d == b) return small_solve_grp<T, a, b>(c, act, Qp, Zrow0, ldz, own0, U, UW, logdet, want_u);
+  if (Nr == a && d == b) \
+    return small_solve_grp<T, a, b>(c, act, Qp, Zrow0, ldz, own0, U, UW, logdet, want_u, want_ld);
   AMM_SS(1, 1)
   AMM_SS(2, 1) AMM_SS(2, 2)
   AMM_SS(3, 1) AMM_SS(3, 2) AMM_SS(3, 3)
@@ -620,32 +621,29 @@ __device__ __forceinline__ void covariance_phase(const InstDesc& D, const Layout
   }
 }
 
-// S3b/S4: FP64 solves, one thread per user, then rho = sum alpha_r R_r
-// (block-uniform).  own-stream block of user r: rows r*Nr.., columns own0..
+// S3b/S4: FP64 solves, four lanes per user, then rho = sum alpha_r R_r
+// (block-uniform; 0 when want_ld is false and the rates are skipped).  own-stream block of user r: rows r*Nr.., columns own0..
 // of the Z view (zrow0(r) gives row r*Nr, ldz its row stride).
 template <class T>
 __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& Ly, const float2* Z, int ldz,
                                               const float2* sQ, float2* sU, float2* sUW, double* sRho,
-                                              const float* alpha_u, bool want_u, double* red, int* fail) {
+                                              const float* alpha_u, bool want_u, bool want_ld, double* red,
+                                              int* fail) {
   const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, np = Ly.np, CK = Ly.CK;
-  // Four lanes per user.  The FP64 units are per SM sub-partition and a
-  // warp instruction costs the same however few lanes are active, so the
-  // users are spread over the first four warps (one per sub-partition)
-  // before any warp takes more: upw users per warp.  The trip count is
-  // warp-uniform (the solve shuffles).
-  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int upw = (CK + 3) >> 2;
-  if (upw > 8) upw = 8;
-  for (int base = 0; base < CK; base += nw * upw) {
-    const int u = lane >> 2, c = lane & 3;
-    const int rr = base + warp * upw + u;
-    const bool act = u < upw && rr < CK;
-    const int r = act ? rr : 0;
+  // Four lanes per user, eight users per warp.  An FP64 warp instruction
+  // costs the same however few of its lanes are active (on this part about
+  // 64 cycles for one warp, and one per 19 cycles for the whole SM), so the
+  // users are packed densely.  The trip count is warp-uniform (the solve
+  // shuffles).
+  for (int base = 0; base < 4 * CK; base += blockDim.x) {
+    const int e = base + threadIdx.x;
+    const bool act = e < 4 * CK;
+    const int r = act ? e >> 2 : 0, c = e & 3;
     if (!__any_sync(0xffffffffu, act)) continue;  // warps without a user skip the (FP64) solve
     const int own0 = (r / K) * n + (r % K) * d;
     double ld = 0.0;
     const bool ok = small_solve_dispatch<T>(Nr, d, c, act, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
-                                            sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u);
+                                            sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u, want_ld);
     if (act && c == 0) {
       if (!ok || !isfinite(ld)) atomicExch(fail, kNumeric);
       sRho[r] = ok ? ld : 0.0;
@@ -701,6 +699,14 @@ __device__ __forceinline__ void gradient_rhs_phase(const InstDesc& D, const Layo
 // Stage test of Algorithm 3 and the stopping test, run by one thread.
 // ctrl: [0] t, [1] stage, [2] stage_iter, [3] last_stage, [4] stop,
 // [6] step flags (bit 0 spectral, bit 1 freeze gamma_c).
+// Whether iteration it of a launch needs R^t = WSR(V^{t-1}): for the stage
+// test (stage I), the tolerance test, and in the last iteration so that a
+// restored state carries rho_prev; inside the latched stage II of a
+// fixed-count run nothing reads it.
+__device__ __forceinline__ bool need_rate(int stage, int mode, int it, int n_iters) {
+  return stage != 2 || mode != kFixed || it + 1 == n_iters;
+}
+
 __device__ __forceinline__ void stage_logic(int* ctrl, double rho, double rho_prev, int mode, float eps1,
                                             float eps2, int switch_iter, int step_rule, int tc) {
   const int t = ctrl[0];

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     covariance_phase(D, Ly, [&](int row, int c) { return Zc[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
     // ---- S3b/S4: FP64 small solves, one thread per user; rho = WSR(V^{t-1})
-    rho = solve_phase<T>(D, Ly, Zc, ldz, sQ, sU, sUW, sRho, alpha_u, p.mode != kEvalWsr, red, &s_fail);
+    rho = solve_phase<T>(D, Ly, Zc, ldz, sQ, sU, sUW, sRho, alpha_u, p.mode != kEvalWsr,
+                         need_rate(s_ctrl[1], p.mode, it, n_iters), red, &s_fail);
     if (s_fail != kOk) break;
     if (p.mode == kEvalWsr) {
       if (tid == 0) p.wsr_out[b] = rho / 0.69314718055994530942;

@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     // ---- S3/S4: covariance, FP64 solves, rho = WSR(V^{t-1}), stage test
     covariance_phase(D, Ly, [&](int row, int c) { return Zs[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
-    rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true, red, &s_fail);
+    rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true,
+                              need_rate(s_ctrl[1], p.mode, it, p.n_iters), red, &s_fail);
     if (s_fail != kOk) break;
     if (tid == 0)
       stage_logic(s_ctrl, rho, s_rhoprev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) wmmse_kernel(IterParams p, float bis
     __syncthreads();
     covariance_phase(D, Ly, [&](int row, int c) { return sZ[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
-    const double rho = solve_phase<double>(D, Ly, sZ, ldz, sQ, sU, sUW, sRho, alpha_u, true, red, &s_fail);
+    const double rho = solve_phase<double>(D, Ly, sZ, ldz, sQ, sU, sUW, sRho, alpha_u, true, true, red, &s_fail);
     if (s_fail != kOk) break;
     // V update per cell, eq. (12)
     for (int k = 0; k < C; ++k) {

@@ -337,6 +337,192 @@ static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, b
   return false;
 }
 
+// FP64 per-user solve by eight lanes: lane (c, p) of the group owns column c
+// and the real (p = 0) or imaginary (p = 1) part.  Every lane keeps the
+// complex factors whole, but each new complex value is computed one part
+// per lane (two FP64 FMAs per complex multiply-add instead of four) and
+// completed by one exchange with the partner lane (lane ^ 4).  An FP64 warp
+// instruction costs the same for any number of active lanes, so halving the
+// per-lane FP64 work halves the phase.  Same algebra as small_solve_grp.
+template <int NR, int DD>
+__device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const float2* Zrow0, int ldz, int own0,
+                                 float2* U, float2* UW, double* logdet, bool want_u, bool want_ld) {
+  typedef Cx<double> C;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, gb = lane & ~7;
+  // s v with s = +1 on the imaginary lane and -1 on the real lane (sign bit flip)
+  const unsigned long long smask = p ? 0ull : 0x8000000000000000ull;
+  auto sg = [&](double v) { return __longlong_as_double(__double_as_longlong(v) ^ (long long)smask); };
+  auto own = [&](C v) { return p ? v.y : v.x; };
+  auto oth = [&](C v) { return p ? v.x : v.y; };
+  auto join = [&](double o) {
+    const double t = __shfl_xor_sync(full, o, 4);
+    return p ? mk<double>(t, o) : mk<double>(o, t);
+  };
+  // own parts: a*b = a.x own(b) + s a.y oth(b); conj(a) b = a.x own(b) - s a.y oth(b);
+  // a conj(b) = -s a.x own(b) + a.y oth(b)
+  bool ok = act;
+  C L[NR][NR];
+  double inv[NR];
+  {
+    C Q[NR][NR];
+    int q = 0;
+#pragma unroll
+    for (int a = 0; a < NR; ++a)
+#pragma unroll
+      for (int b = a; b < NR; ++b) {
+        const float2 v = act ? Qp[q] : make_float2(a == b ? 1.f : 0.f, 0.f);
+        Q[a][b] = join((double)(p ? v.y : v.x));
+        Q[b][a] = cj(Q[a][b]);
+        ++q;
+      }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < j; ++k) acc = fma(own(L[j][k]), own(L[j][k]), acc);
+      acc += __shfl_xor_sync(full, acc, 4);
+      double dj = Q[j][j].x - acc;
+      if (!(dj > 0.0)) {
+        ok = false;
+        dj = 1.0;
+      }
+      const double rj = rsqrt(dj);
+      inv[j] = rj;
+      L[j][j] = mk<double>(dj * rj, 0.0);
+#pragma unroll
+      for (int i = j + 1; i < NR; ++i) {
+        double t = own(Q[i][j]);
+#pragma unroll
+        for (int k = 0; k < j; ++k) t = fma(sg(L[i][k].x), own(L[j][k]), fma(-L[i][k].y, oth(L[j][k]), t));
+        L[i][j] = join(t * rj);
+      }
+    }
+  }
+  // this lane's column of X = L^{-1} Z_own
+  const bool mine = act && c < DD;
+  C x[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const float2 zv = mine ? Zrow0[(long long)i * ldz + own0 + c] : make_float2(0.f, 0.f);
+    double t = (double)(p ? zv.y : zv.x);
+#pragma unroll
+    for (int k = 0; k < i; ++k) t = fma(-L[i][k].x, own(x[k]), fma(-sg(L[i][k].y), oth(x[k]), t));
+    x[i] = join(t * inv[i]);
+  }
+  // column c of M = X^H X, then every lane gathers M and factors I + M = R R^H
+  C mcol[DD];
+#pragma unroll
+  for (int a = 0; a < DD; ++a) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int src = gb + 4 * p + a;
+      const C xa = mk<double>(__shfl_sync(full, x[i].x, src), __shfl_sync(full, x[i].y, src));
+      t = fma(xa.x, own(x[i]), fma(-sg(xa.y), oth(x[i]), t));
+    }
+    mcol[a] = join(t);
+  }
+  C R[DD][DD];
+  double rinv[DD];
+  double mypiv = 0.0;
+  {
+    C A[DD][DD];
+#pragma unroll
+    for (int b = 0; b < DD; ++b)
+#pragma unroll
+      for (int a = 0; a < DD; ++a) {
+        const int src = gb + 4 * p + b;
+        A[a][b] = mk<double>(__shfl_sync(full, mcol[a].x, src), __shfl_sync(full, mcol[a].y, src));
+      }
+#pragma unroll
+    for (int j = 0; j < DD; ++j) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < j; ++k) acc = fma(own(R[j][k]), own(R[j][k]), acc);
+      acc += __shfl_xor_sync(full, acc, 4);
+      double dm1 = A[j][j].x - acc;  // pivot - 1
+      if (!(dm1 > -1.0)) {
+        ok = false;
+        dm1 = 0.0;
+      }
+      if (j == c) mypiv = dm1;
+      const double dj = 1.0 + dm1;
+      const double rj = rsqrt(dj);
+      rinv[j] = rj;
+      R[j][j] = mk<double>(dj * rj, 0.0);
+#pragma unroll
+      for (int i = j + 1; i < DD; ++i) {
+        double t = own(A[i][j]);
+#pragma unroll
+        for (int k = 0; k < j; ++k) t = fma(sg(R[i][k].x), own(R[j][k]), fma(-R[i][k].y, oth(R[j][k]), t));
+        R[i][j] = join(t * rj);
+      }
+    }
+  }
+  // log det(I + M): lane c contributes log1p of pivot c, summed over the columns
+  double ld = (want_ld && c < DD) ? log1p(mypiv) : 0.0;
+  ld += __shfl_xor_sync(full, ld, 1);
+  ld += __shfl_xor_sync(full, ld, 2);
+  if (c == 0 && p == 0) *logdet = ld;
+  if (!want_u) return ok;
+  // this lane's column of UW = L^{-H} x
+  C y[NR];
+#pragma unroll
+  for (int i = NR - 1; i >= 0; --i) {
+    double t = own(x[i]);
+#pragma unroll
+    for (int k = i + 1; k < NR; ++k) t = fma(-L[k][i].x, own(y[k]), fma(sg(L[k][i].y), oth(y[k]), t));
+    y[i] = join(t * inv[i]);
+  }
+  // column c of (I+M)^{-1}: R g = e_c, then R^H m = g
+  C g[DD], mi[DD];
+#pragma unroll
+  for (int i = 0; i < DD; ++i) {
+    double t = (p == 0 && i == c) ? 1.0 : 0.0;
+#pragma unroll
+    for (int k = 0; k < i; ++k) t = fma(-R[i][k].x, own(g[k]), fma(-sg(R[i][k].y), oth(g[k]), t));
+    g[i] = join(t * rinv[i]);
+  }
+#pragma unroll
+  for (int i = DD - 1; i >= 0; --i) {
+    double t = own(g[i]);
+#pragma unroll
+    for (int k = i + 1; k < DD; ++k) t = fma(-R[k][i].x, own(mi[k]), fma(sg(R[k][i].y), oth(mi[k]), t));
+    mi[i] = join(t * rinv[i]);
+  }
+  // U[:, c] = sum_b UW[:, b] (I+M)^{-1}[b][c]; each lane stores its part
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    double t = 0.0;
+#pragma unroll
+    for (int b = 0; b < DD; ++b) {
+      const int src = gb + 4 * p + b;
+      const C uw = mk<double>(__shfl_sync(full, y[i].x, src), __shfl_sync(full, y[i].y, src));
+      t = fma(uw.x, own(mi[b]), fma(sg(uw.y), oth(mi[b]), t));
+    }
+    if (mine && ok) {
+      reinterpret_cast<float*>(U + i * DD + c)[p] = (float)t;
+      reinterpret_cast<float*>(UW + i * DD + c)[p] = (float)own(y[i]);
+    }
+  }
+  return ok;
+}
+
+static __device__ __noinline__ bool small_solve_pair_dispatch(int Nr, int d, int c, int p, bool act,
+                                                              const float2* Qp, const float2* Zrow0, int ldz,
+                                                              int own0, float2* U, float2* UW, double* logdet,
+                                                              bool want_u, bool want_ld) {
+#define AMM_SP(a, b) \
+  if (Nr == a && d == b) return small_solve_pair<a, b>(c, p, act, Qp, Zrow0, ldz, own0, U, UW, logdet, want_u, want_ld);
+  AMM_SP(1, 1)
+  AMM_SP(2, 1) AMM_SP(2, 2)
+  AMM_SP(3, 1) AMM_SP(3, 2) AMM_SP(3, 3)
+  AMM_SP(4, 1) AMM_SP(4, 2) AMM_SP(4, 3) AMM_SP(4, 4)
+#undef AMM_SP
+  return false;
+}
+
 // ------------------------------------------------------- Lanczos ||F_k||_2
 // Number of eigenvalues of the symmetric tridiagonal T (diagonal a,
 // off-diagonal b, order n) below x: the negative pivots of T - x I (Sturm
@@ -630,21 +816,28 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
                                               const float* alpha_u, bool want_u, bool want_ld, double* red,
                                               int* fail) {
   const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, np = Ly.np, CK = Ly.CK;
-  // Four lanes per user, eight users per warp.  An FP64 warp instruction
-  // costs the same however few of its lanes are active (on this part about
-  // 64 cycles for one warp, and one per 19 cycles for the whole SM), so the
-  // users are packed densely.  The trip count is warp-uniform (the solve
+  // An FP64 warp instruction costs the same however few of its lanes are
+  // active (on this part about 64 cycles for one warp, and one per 19 cycles
+  // for the whole SM), so the users are packed densely: FP64 solves take
+  // eight lanes per user (column x real/imaginary part, small_solve_pair),
+  // FP32 solves four (column).  The trip count is warp-uniform (the solve
   // shuffles).
-  for (int base = 0; base < 4 * CK; base += blockDim.x) {
+  constexpr int kLanes = sizeof(T) == 8 ? 8 : 4;
+  for (int base = 0; base < kLanes * CK; base += blockDim.x) {
     const int e = base + threadIdx.x;
-    const bool act = e < 4 * CK;
-    const int r = act ? e >> 2 : 0, c = e & 3;
-    if (!__any_sync(0xffffffffu, act)) continue;  // warps without a user skip the (FP64) solve
+    const bool act = e < kLanes * CK;
+    const int r = act ? e / kLanes : 0, c = e & 3, ri = (e / 4) & (kLanes / 4 - 1);
+    if (!__any_sync(0xffffffffu, act)) continue;  // warps without a user skip the solve
     const int own0 = (r / K) * n + (r % K) * d;
     double ld = 0.0;
-    const bool ok = small_solve_dispatch<T>(Nr, d, c, act, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
-                                            sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u, want_ld);
-    if (act && c == 0) {
+    bool ok;
+    if (kLanes == 8)
+      ok = small_solve_pair_dispatch(Nr, d, c, ri, act, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
+                                     sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u, want_ld);
+    else
+      ok = small_solve_dispatch<T>(Nr, d, c, act, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
+                                   sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u, want_ld);
+    if (act && c == 0 && ri == 0) {
       if (!ok || !isfinite(ld)) atomicExch(fail, kNumeric);
       sRho[r] = ok ? ld : 0.0;
     }

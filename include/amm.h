@@ -247,6 +247,60 @@ AMM_API const char* amm_last_error(const amm_ctx* ctx);
 /* Number of kernel launches this context has issued, for launch accounting. */
 AMM_API int64_t amm_launch_count(const amm_ctx* ctx);
 
+/* ---------------------------------------------------------------------
+ * Differentiable unrolled A-MMMSE.
+ *
+ * T iterations of Algorithm 3 (Sec. V, eqs. (9), (10), (13)-(18)) in which
+ * the step of iteration t is a parameter gamma_t (eq. (16) replaced by a
+ * learnable schedule shared by the batch) and the stage schedule is fixed:
+ * stage I (W = I) before iteration switch_iter, stage II (W = E^{-1}, eq.
+ * (10)) from it on (switch_iter < 1: stage I throughout).  U^t is taken at
+ * V^{t-1}, the gradient at the extrapolated point with omega^t of eq. (18)
+ * (extrapolate = 0: omega = 0), and V^t is projected onto the power ball
+ * (eq. (15)).  The output is WSR(V^T) in bits.  A hand-written adjoint
+ * returns its gradient with respect to every gamma_t and to H.  The paper
+ * unrolls nothing; this is the differentiable variant of its iteration.
+ *
+ * One cell per instance (dims.cells = 1), a uniform batch, every instance's
+ * working set in shared memory (AMM_EUNSUPPORTED otherwise).  The forward
+ * pass keeps (V^{c-1}, V^c) every ckpt_every iterations; the backward pass
+ * recomputes each segment from its checkpoint.
+ * ------------------------------------------------------------------- */
+typedef struct amm_unrolled amm_unrolled;
+
+/* Create an unrolled solver for `batch` instances of sizes *dims, T
+ * iterations, checkpoints every ckpt_every iterations; work is queued on
+ * `stream` (a cudaStream_t; NULL = legacy default stream).  Allocates the
+ * checkpoint and recomputation workspace. */
+AMM_API amm_status amm_unrolled_create(amm_unrolled** out, int batch, const amm_dims* dims, int T, int ckpt_every,
+                                       int switch_iter, int extrapolate, void* stream);
+
+/* Forward pass.  Device inputs, caller-owned, read again by the backward
+ * pass (keep them alive and unchanged until it has run): H (complex64, batch
+ * x K Nr x Nt, the amm_set_problem layout for one cell), alpha and sigma2
+ * (float, batch x K), P (float, batch), V0 (complex64, batch x Nt x K d; a
+ * feasible start, e.g. the projected warm start of eq. (15)), gamma (float,
+ * T).  Output wsr (double, batch, bits).  Channels are normalised by sigma
+ * inside, as in amm_set_problem.  Asynchronous. */
+AMM_API amm_status amm_unrolled_forward(amm_unrolled* u, const void* H, const float* alpha, const float* sigma2,
+                                        const float* P, const void* V0, const float* gamma, double* wsr);
+
+/* Backward pass for the last forward pass: wsr_bar (double, batch) holds
+ * dL/dWSR per instance; outputs gamma_bar (float, batch x T: instance b's
+ * dL/dgamma_t, summed over b by the caller) and H_bar (complex64, the layout
+ * of H: dL/dRe(H) + i dL/dIm(H)).  Asynchronous. */
+AMM_API amm_status amm_unrolled_backward(amm_unrolled* u, const double* wsr_bar, float* gamma_bar, void* H_bar);
+
+/* Per-instance status of the last pass (AMM_OK or AMM_ENUMERIC) into a
+ * device int array of batch entries. */
+AMM_API amm_status amm_unrolled_status(amm_unrolled* u, int* status_dev);
+
+/* Message of the last error on u (or of the last failed create when u is NULL). */
+AMM_API const char* amm_unrolled_last_error(amm_unrolled* u);
+
+/* Release u and its workspace. */
+AMM_API void amm_unrolled_destroy(amm_unrolled* u);
+
 #ifdef __cplusplus
 }
 #endif

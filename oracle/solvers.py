@@ -233,3 +233,20 @@ def wmmse(H, sigma2, alpha, P, K, Nr, d, V0, iters: int, tol: float = 1e-4,
         if eps is not None and m.relative_change(hist[-1], hist[-2]) <= eps:
             break
     return V, hist, it
+
+
+# --------------------------------------------------- unrolled A-MMMSE
+def ammmse_unrolled(H, sigma2, alpha, P, K, Nr, d, V0, gammas, switch_iter: int,
+                    extrapolate: bool = True):
+    """T = len(gammas) iterations of Algorithm 3 with the step of iteration
+    t fixed to gammas[t-1] (the same for every cell) and the stage schedule
+    fixed: stage I before iteration switch_iter, stage II from it on (the
+    unrolled network of the differentiable variant; every other step as in
+    ammmse_iteration); switch_iter < 1 keeps stage I throughout.  Returns
+    (V^T, WSR(V^T) in bits)."""
+    st = AState(V=V0.copy(), Vprev=V0.copy())
+    sw = switch_iter if switch_iter >= 1 else len(gammas) + 1
+    for g in gammas:
+        opt = Options(step_rule=2, gamma_c=float(g), switch_iter=sw, extrapolate=extrapolate)
+        ammmse_iteration(H, sigma2, alpha, P, K, Nr, d, st, opt)
+    return st.V, m.wsr_bits(H, st.V, sigma2, alpha, K, Nr, d)

@@ -48,7 +48,8 @@ class State(ctypes.Structure):
 EXPORTS = ["amm_default_opts", "amm_create", "amm_sizes", "amm_set_problem", "amm_warmstart", "amm_step",
            "amm_solve", "amm_wsr", "amm_wmmse_step", "amm_get_V", "amm_get_state", "amm_set_state",
            "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count",
-           "amm_solve_noalloc"]
+           "amm_solve_noalloc", "amm_unrolled_create", "amm_unrolled_forward", "amm_unrolled_backward",
+           "amm_unrolled_status", "amm_unrolled_last_error", "amm_unrolled_destroy"]
 
 _lib = None
 
@@ -84,6 +85,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "amm_launch_count": (i64, [vp]),
         "amm_solve_noalloc": (i32, [i32, ctypes.POINTER(Dims), ctypes.POINTER(Opts), vp, vp, vp, vp, vp, i32, vp,
                                     vp, vp, ctypes.c_char_p, i32]),
+        "amm_unrolled_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(Dims), i32, i32, i32, i32, vp]),
+        "amm_unrolled_forward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "amm_unrolled_backward": (i32, [vp, vp, vp, vp]),
+        "amm_unrolled_status": (i32, [vp, vp]),
+        "amm_unrolled_last_error": (ctypes.c_char_p, [vp]),
+        "amm_unrolled_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -237,3 +244,50 @@ class Solver:
     @property
     def launches(self) -> int:
         return int(self.lib.amm_launch_count(self.h))
+
+
+class UnrolledSolver:
+    """The differentiable unrolled A-MMMSE of include/amm.h (amm_unrolled_*):
+    T iterations with step sizes gamma_t and a fixed stage schedule, its
+    WSR(V^T) and the hand-written adjoint.  One cell per instance."""
+
+    def __init__(self, batch: int, dims, T: int, ckpt_every: int = 5, switch_iter: int = -1,
+                 extrapolate: bool = True, stream=None):
+        self.lib = load_library()
+        d = Dims(*dims)
+        h = ctypes.c_void_p()
+        st = self.lib.amm_unrolled_create(ctypes.byref(h), batch, ctypes.byref(d), T, ckpt_every, switch_iter,
+                                          1 if extrapolate else 0, _stream_handle(stream))
+        if st != AMM_OK:
+            raise AmmError(st, self.lib.amm_unrolled_last_error(None).decode())
+        self.h = h
+        self.batch, self.dims, self.T = batch, tuple(dims), T
+        self._keep = None
+
+    def _check(self, st: int):
+        if st != AMM_OK:
+            raise AmmError(st, self.lib.amm_unrolled_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.amm_unrolled_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, H, alpha, sigma2, P, V0, gamma, wsr_out):
+        self._keep = (H, alpha, sigma2, P, V0, gamma)  # read again by backward
+        self._check(self.lib.amm_unrolled_forward(self.h, _ptr(H), _ptr(alpha), _ptr(sigma2), _ptr(P), _ptr(V0),
+                                                  _ptr(gamma), _ptr(wsr_out)))
+        return wsr_out
+
+    def backward(self, wsr_bar, gamma_bar, H_bar):
+        self._check(self.lib.amm_unrolled_backward(self.h, _ptr(wsr_bar), _ptr(gamma_bar), _ptr(H_bar)))
+
+    def status(self, out):
+        self._check(self.lib.amm_unrolled_status(self.h, _ptr(out)))
+        return out

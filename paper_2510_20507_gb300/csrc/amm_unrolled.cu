@@ -1,0 +1,781 @@
+// Differentiable unrolled A-MMMSE: T iterations of Algorithm 3 with the
+// step of iteration t a parameter gamma_t (shared by the batch) and the stage
+// schedule fixed (stage I before iteration switch_iter, stage II from it on),
+// and a hand-written adjoint that returns the gradient of WSR(V^T) with
+// respect to every gamma_t and to the channels H.
+//
+// One block per instance, single cell (C = 1), everything in shared memory.
+// The forward pass keeps (V^{c-1}, V^c) at every ck-th iteration; the
+// backward pass recomputes each segment of ck iterations from its checkpoint
+// and runs the adjoint of the iteration backwards through it.  Complex
+// matrices are FP32; the per-user Nr x Nr / d x d Hermitian solves are FP64.
+//
+// Gradients use the real-gradient convention for complex variables: for a
+// real L and complex X, Xbar = dL/dRe(X) + i dL/dIm(X), so that
+// dL = Re tr(Xbar^H dX).  With it, the adjoint of C = A B is
+// Abar = Cbar B^H, Bbar = A^H Cbar, and the gradient of the WMMSE objective
+// f (eq. (8)) in V is G = H^H Y with Y_r = 2 alpha_r U_r W_r (U_r^H Z_r - S_r)
+// (eq. (14) in matrix-free form).  At the MMSE receiver and W = E^{-1},
+// WSR(V) = sum_r alpha_r d - min_{U,W} f, so by the envelope theorem the
+// WSR's gradient is -G in V and -Y V^H in H.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/amm.h"
+#include "amm_internal.cuh"
+
+namespace amm {
+namespace {
+
+constexpr int kUThreads = 256;
+
+// Byte offsets of the shared-memory buffers of one instance.
+struct ULayout {
+  int H, Va, Vb, Vh, G, B, A1, A2, A3, Hb, Z, Zh, Y, Yb, Zb, Zhb;
+  int Ti, U, W, P, Ub, Pb, red, ld, total;
+};
+
+__host__ __device__ inline int u_take(int& off, int bytes) {
+  const int o = off;
+  off = (off + bytes + 15) & ~15;
+  return o;
+}
+
+__host__ __device__ inline ULayout u_layout(int K, int Nt, int Nr, int d) {
+  const int m = K * Nr, n = K * d, vb = Nt * n * 8, zb = m * n * 8, hb = m * Nt * 8;
+  ULayout L;
+  int off = 0;
+  L.H = u_take(off, hb);
+  L.Va = u_take(off, vb);
+  L.Vb = u_take(off, vb);
+  L.Vh = u_take(off, vb);
+  L.G = u_take(off, vb);
+  L.B = u_take(off, vb);
+  L.A1 = u_take(off, vb);
+  L.A2 = u_take(off, vb);
+  L.A3 = u_take(off, vb);
+  L.Hb = u_take(off, hb);
+  L.Z = u_take(off, zb);
+  L.Zh = u_take(off, zb);
+  L.Y = u_take(off, zb);
+  L.Yb = u_take(off, zb);
+  L.Zb = u_take(off, zb);
+  L.Zhb = u_take(off, zb);
+  L.Ti = u_take(off, K * Nr * Nr * 8);
+  L.U = u_take(off, K * Nr * d * 8);
+  L.W = u_take(off, K * d * d * 8);
+  L.P = u_take(off, K * Nr * d * 8);
+  L.Ub = u_take(off, K * Nr * d * 8);
+  L.Pb = u_take(off, K * Nr * d * 8);
+  L.red = u_take(off, 66 * 8);
+  L.ld = u_take(off, K * 8);
+  L.total = off;
+  return L;
+}
+
+struct UParams {
+  int batch, K, Nt, Nr, d, T, ck, nseg, switch_iter, extrapolate;
+  const float2* H;        // batch x m x Nt (as given)
+  const float* sigma2;    // batch x K
+  const float* alpha;     // batch x K
+  const float* P;         // batch
+  const float2* V0;       // batch x Nt x n
+  const float* gamma;     // T
+  float2* ckpt;           // batch x (2 nseg + 1) x Nt x n
+  float2* hist;           // batch x (ck + 2) x Nt x n
+  double* wsr;            // batch, bits
+  const double* wsr_bar;  // batch
+  float* gamma_bar;       // batch x T
+  float2* H_bar;          // batch x m x Nt
+  int* status;            // batch
+};
+
+// C(r, c) = sum_p a(r, p) b(p, c), one thread per output element.
+template <class AG, class BG, class EP>
+__device__ __forceinline__ void u_gemm(int M, int N, int KK, AG a, BG b, EP ep) {
+  for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
+    const int r = e / N, c = e - r * N;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int p = 0; p < KK; ++p) acc = cfma(a(r, p), b(p, c), acc);
+    ep(r, c, acc);
+  }
+}
+
+struct UView {
+  int K, Nt, Nr, d, m, n;
+  float2 *H, *Z, *Zh, *Y, *G, *Ti, *U, *W, *P;
+  double* ld;  // per user: log det E_r
+  const float* alpha;
+};
+
+// ---- FP64 helpers on small row-major complex matrices (one thread)
+struct Z64 {
+  double x, y;
+};
+__device__ __forceinline__ Z64 zmk(double x, double y) {
+  Z64 r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+__device__ __forceinline__ Z64 zld(float2 v) { return zmk((double)v.x, (double)v.y); }
+__device__ __forceinline__ Z64 zmul(Z64 a, Z64 b) { return zmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ Z64 zcmul(Z64 a, Z64 b) { return zmk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a) b
+__device__ __forceinline__ Z64 zadd(Z64 a, Z64 b) { return zmk(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ Z64 zsub(Z64 a, Z64 b) { return zmk(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 zst(Z64 a) { return make_float2((float)a.x, (float)a.y); }
+
+// Cholesky A = L L^H of an n x n Hermitian matrix (lower triangle of A
+// read); returns false on a non-positive pivot.  logdet += log det A.
+__device__ bool z_chol(const Z64* A, Z64* L, int n, double* logdet) {
+  for (int j = 0; j < n; ++j) {
+    double dj = A[j * n + j].x;
+    for (int k = 0; k < j; ++k) dj -= L[j * n + k].x * L[j * n + k].x + L[j * n + k].y * L[j * n + k].y;
+    if (!(dj > 0.0)) return false;
+    const double lj = sqrt(dj);
+    *logdet += log(dj);
+    L[j * n + j] = zmk(lj, 0.0);
+    for (int i = j + 1; i < n; ++i) {
+      Z64 s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s = zsub(s, zmul(L[i * n + k], zmk(L[j * n + k].x, -L[j * n + k].y)));
+      L[i * n + j] = zmk(s.x / lj, s.y / lj);
+    }
+    for (int i = 0; i < j; ++i) L[i * n + j] = zmk(0.0, 0.0);
+  }
+  return true;
+}
+
+// X = A^{-1} B for A = L L^H (n x n), B n x k, all row-major.
+__device__ void z_chol_solve(const Z64* L, int n, const Z64* B, int k, Z64* X) {
+  for (int c = 0; c < k; ++c) {
+    for (int i = 0; i < n; ++i) {  // L y = b
+      Z64 s = B[i * k + c];
+      for (int j = 0; j < i; ++j) s = zsub(s, zmul(L[i * n + j], X[j * k + c]));
+      X[i * k + c] = zmk(s.x / L[i * n + i].x, s.y / L[i * n + i].x);
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^H x = y
+      Z64 s = X[i * k + c];
+      for (int j = i + 1; j < n; ++j) s = zsub(s, zcmul(L[j * n + i], X[j * k + c]));
+      X[i * k + c] = zmk(s.x / L[i * n + i].x, s.y / L[i * n + i].x);
+    }
+  }
+}
+
+// Per-user solves of one iteration (thread r < K), from Z = H V^{t-1}:
+// T_r = I + Z_r Z_r^H (all columns), U_r = T_r^{-1} Z_own (eq. (9), sigma^2 = 1),
+// E_r = I - U_r^H Z_own, W_r = E_r^{-1} (eq. (10); I in stage I), P_r = U_r W_r.
+// Stores T_r^{-1}, U, W, P and log det E_r.  Returns false on a failed factorisation.
+__device__ bool u_solve_user(const UView& X, int r, bool stage2) {
+  const int Nr = X.Nr, d = X.d, n = X.n;
+  Z64 A[16], L[16], I4[16], Ti[16], Zo[16], Uu[16], E[16], Le[16], Wm[16];
+  for (int a = 0; a < Nr; ++a)
+    for (int b = 0; b < Nr; ++b) {
+      Z64 s = zmk(a == b ? 1.0 : 0.0, 0.0);
+      for (int c = 0; c < n; ++c) {
+        const Z64 za = zld(X.Z[(r * Nr + a) * n + c]), zb = zld(X.Z[(r * Nr + b) * n + c]);
+        s = zadd(s, zcmul(zb, za));  // z_a conj(z_b)
+      }
+      A[a * Nr + b] = s;
+      I4[a * Nr + b] = zmk(a == b ? 1.0 : 0.0, 0.0);
+    }
+  double ldT = 0.0;
+  if (!z_chol(A, L, Nr, &ldT)) return false;
+  z_chol_solve(L, Nr, I4, Nr, Ti);
+  for (int a = 0; a < Nr; ++a)
+    for (int s = 0; s < d; ++s) Zo[a * d + s] = zld(X.Z[(r * Nr + a) * n + r * d + s]);
+  for (int a = 0; a < Nr; ++a)
+    for (int s = 0; s < d; ++s) {
+      Z64 acc = zmk(0.0, 0.0);
+      for (int b = 0; b < Nr; ++b) acc = zadd(acc, zmul(Ti[a * Nr + b], Zo[b * d + s]));
+      Uu[a * d + s] = acc;
+    }
+  for (int s = 0; s < d; ++s)
+    for (int u = 0; u < d; ++u) {
+      Z64 acc = zmk(s == u ? 1.0 : 0.0, 0.0);
+      for (int a = 0; a < Nr; ++a) acc = zsub(acc, zcmul(Uu[a * d + s], Zo[a * d + u]));
+      E[s * d + u] = acc;
+    }
+  for (int s = 0; s < d; ++s)  // Hermitian part
+    for (int u = s; u < d; ++u) {
+      const Z64 h = zmk(0.5 * (E[s * d + u].x + E[u * d + s].x), 0.5 * (E[s * d + u].y - E[u * d + s].y));
+      E[s * d + u] = h;
+      E[u * d + s] = zmk(h.x, -h.y);
+    }
+  double ldE = 0.0;
+  if (!z_chol(E, Le, d, &ldE)) return false;
+  for (int s = 0; s < d; ++s)
+    for (int u = 0; u < d; ++u) I4[s * d + u] = zmk(s == u ? 1.0 : 0.0, 0.0);
+  if (stage2) {
+    z_chol_solve(Le, d, I4, d, Wm);
+  } else {
+    for (int q = 0; q < d * d; ++q) Wm[q] = I4[q];
+  }
+  for (int q = 0; q < Nr * Nr; ++q) X.Ti[r * Nr * Nr + q] = zst(Ti[q]);
+  for (int q = 0; q < Nr * d; ++q) X.U[r * Nr * d + q] = zst(Uu[q]);
+  for (int q = 0; q < d * d; ++q) X.W[r * d * d + q] = zst(Wm[q]);
+  for (int a = 0; a < Nr; ++a)
+    for (int s = 0; s < d; ++s) {
+      Z64 acc = zmk(0.0, 0.0);
+      for (int u = 0; u < d; ++u) acc = zadd(acc, zmul(Uu[a * d + u], Wm[u * d + s]));
+      X.P[(r * Nr + a) * d + s] = zst(acc);
+    }
+  X.ld[r] = ldE;
+  return true;
+}
+
+// Forward part of iteration t shared by both passes: Z = H Va, the per-user
+// solves, Vh = Vhat, Zh = H Vhat, Y (eq. (14) form) and G = H^H Y.
+__device__ void u_forward_iter(const UView& X, bool stage2, float omega, const float2* Va, const float2* Vb,
+                               float2* Vh, int* fail) {
+  const int m = X.m, n = X.n, Nt = X.Nt, Nr = X.Nr, d = X.d, K = X.K;
+  u_gemm(m, n, Nt, [&](int r, int p) { return X.H[r * Nt + p]; }, [&](int p, int c) { return Va[p * n + c]; },
+         [&](int r, int c, float2 v) { X.Z[r * n + c] = v; });
+  for (int e = threadIdx.x; e < Nt * n; e += blockDim.x)
+    Vh[e] = make_float2((1.f + omega) * Va[e].x - omega * Vb[e].x, (1.f + omega) * Va[e].y - omega * Vb[e].y);
+  __syncthreads();
+  for (int r = threadIdx.x; r < K; r += blockDim.x)
+    if (!u_solve_user(X, r, stage2)) atomicExch(fail, kNumeric);
+  u_gemm(m, n, Nt, [&](int r, int p) { return X.H[r * Nt + p]; }, [&](int p, int c) { return Vh[p * n + c]; },
+         [&](int r, int c, float2 v) { X.Zh[r * n + c] = v; });
+  __syncthreads();
+  // Y_r = 2 alpha_r P_r (U_r^H Zh_r - S_r), one thread per (user, column)
+  for (int e = threadIdx.x; e < K * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    float2 As[kMaxNr];
+    for (int s = 0; s < d; ++s) {
+      float2 acc = make_float2(c == r * d + s ? -1.f : 0.f, 0.f);
+      for (int b = 0; b < Nr; ++b) acc = cjfma(X.U[(r * Nr + b) * d + s], X.Zh[(r * Nr + b) * n + c], acc);
+      As[s] = acc;
+    }
+    const float a2 = 2.f * X.alpha[r];
+    for (int a = 0; a < Nr; ++a) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int s = 0; s < d; ++s) acc = cfma(X.P[(r * Nr + a) * d + s], As[s], acc);
+      X.Y[(r * Nr + a) * n + c] = cscale(acc, a2);
+    }
+  }
+  __syncthreads();
+  u_gemm(Nt, n, m, [&](int q, int i) { return make_float2(X.H[i * Nt + q].x, -X.H[i * Nt + q].y); },
+         [&](int i, int c) { return X.Y[i * n + c]; }, [&](int q, int c, float2 v) { X.G[q * n + c] = v; });
+  __syncthreads();
+}
+
+__device__ __forceinline__ float u_omega(const UParams& p, int t) {
+  return (p.extrapolate && t >= 3) ? (float)(t - 2) / (float)(t + 1) : 0.f;
+}
+
+__device__ __forceinline__ float2* u_ckpt(const UParams& p, int b, int slot) {
+  const long long vn = (long long)p.Nt * p.K * p.d;
+  return p.ckpt + ((long long)b * (2 * p.nseg + 1) + slot) * vn;
+}
+
+__device__ UView u_view(const UParams& p, unsigned char* smem, const ULayout& L, int b) {
+  UView X;
+  X.K = p.K;
+  X.Nt = p.Nt;
+  X.Nr = p.Nr;
+  X.d = p.d;
+  X.m = p.K * p.Nr;
+  X.n = p.K * p.d;
+  X.H = reinterpret_cast<float2*>(smem + L.H);
+  X.Z = reinterpret_cast<float2*>(smem + L.Z);
+  X.Zh = reinterpret_cast<float2*>(smem + L.Zh);
+  X.Y = reinterpret_cast<float2*>(smem + L.Y);
+  X.G = reinterpret_cast<float2*>(smem + L.G);
+  X.Ti = reinterpret_cast<float2*>(smem + L.Ti);
+  X.U = reinterpret_cast<float2*>(smem + L.U);
+  X.W = reinterpret_cast<float2*>(smem + L.W);
+  X.P = reinterpret_cast<float2*>(smem + L.P);
+  X.ld = reinterpret_cast<double*>(smem + L.ld);
+  X.alpha = p.alpha + (long long)b * p.K;
+  return X;
+}
+
+// H_n = H / sigma_r per user row
+__device__ void u_load_h(const UParams& p, const UView& X, int b) {
+  const float2* Hg = p.H + (long long)b * X.m * X.Nt;
+  for (int e = threadIdx.x; e < X.m * X.Nt; e += blockDim.x) {
+    const int i = e / X.Nt;
+    const float is = rsqrtf(p.sigma2[(long long)b * X.K + i / X.Nr]);
+    X.H[e] = cscale(Hg[e], is);
+  }
+}
+
+// V^t = project(Vh - gamma G) into out; returns ||Vh - gamma G||^2
+__device__ double u_step_project(const UView& X, float gam, float Pc, const float2* Vh, float2* out, double* red) {
+  const int N = X.Nt * X.n;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const float2 v = make_float2(Vh[e].x - gam * X.G[e].x, Vh[e].y - gam * X.G[e].y);
+    s += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  s = block_sum(s, red);
+  const float sc = (s > (double)Pc) ? (float)sqrt((double)Pc / s) : 1.f;
+  for (int e = threadIdx.x; e < N; e += blockDim.x)
+    out[e] = make_float2((Vh[e].x - gam * X.G[e].x) * sc, (Vh[e].y - gam * X.G[e].y) * sc);
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(kUThreads) u_forward_kernel(UParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_fail;
+  const int b = blockIdx.x;
+  const ULayout L = u_layout(p.K, p.Nt, p.Nr, p.d);
+  const UView X = u_view(p, smem, L, b);
+  double* red = reinterpret_cast<double*>(smem + L.red);
+  if (threadIdx.x == 0) s_fail = kOk;
+  float2* Vbuf[3] = {reinterpret_cast<float2*>(smem + L.Va), reinterpret_cast<float2*>(smem + L.Vb),
+                     reinterpret_cast<float2*>(smem + L.B)};
+  float2* Vh = reinterpret_cast<float2*>(smem + L.Vh);
+  const int N = X.Nt * X.n;
+  u_load_h(p, X, b);
+  const float2* V0 = p.V0 + (long long)b * N;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) Vbuf[0][e] = Vbuf[1][e] = V0[e];
+  __syncthreads();
+  const float Pc = p.P[b];
+  int ia = 0, ib = 1, in = 2;  // V^{t-1}, V^{t-2}, free
+  for (int t = 1; t <= p.T; ++t) {
+    if ((t - 1) % p.ck == 0) {
+      const int sgi = (t - 1) / p.ck;
+      float2* c0 = u_ckpt(p, b, 2 * sgi);
+      float2* c1 = u_ckpt(p, b, 2 * sgi + 1);
+      for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        c0[e] = Vbuf[ib][e];
+        c1[e] = Vbuf[ia][e];
+      }
+    }
+    const bool stage2 = p.switch_iter >= 1 && t >= p.switch_iter;
+    u_forward_iter(X, stage2, u_omega(p, t), Vbuf[ia], Vbuf[ib], Vh, &s_fail);
+    u_step_project(X, p.gamma[t - 1], Pc, Vh, Vbuf[in], red);
+    const int old_b = ib;
+    ib = ia;
+    ia = in;
+    in = old_b;
+  }
+  // V^T and WSR(V^T) = sum_r alpha_r log det E_r^{-1} at the MMSE receiver
+  float2* cT = u_ckpt(p, b, 2 * p.nseg);
+  for (int e = threadIdx.x; e < N; e += blockDim.x) cT[e] = Vbuf[ia][e];
+  u_forward_iter(X, true, 0.f, Vbuf[ia], Vbuf[ia], Vh, &s_fail);
+  double part = 0.0;
+  for (int r = threadIdx.x; r < X.K; r += blockDim.x) part += (double)X.alpha[r] * (-X.ld[r]);
+  const double w = block_sum(part, red);
+  if (threadIdx.x == 0) {
+    p.wsr[b] = w / 0.69314718055994530942;
+    p.status[b] = s_fail;
+  }
+}
+
+// Adjoint of one iteration t.  In: A1 = Vbar^t (complete), A2 = the part of
+// Vbar^{t-1} already collected.  Out: A2 += this iteration's share of
+// Vbar^{t-1}, A3 = its share of Vbar^{t-2}, Hb += its share of Hbar,
+// gamma_bar[t-1].
+__device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& L, unsigned char* smem, int b, int t,
+                               const float2* Va, const float2* Vb, const float2* A1, float2* A2, float2* A3,
+                               int* fail) {
+  const int m = X.m, n = X.n, Nt = X.Nt, Nr = X.Nr, d = X.d, K = X.K, N = Nt * n;
+  double* red = reinterpret_cast<double*>(smem + L.red);
+  float2* Vh = reinterpret_cast<float2*>(smem + L.Vh);
+  float2* B = reinterpret_cast<float2*>(smem + L.B);
+  float2* Hb = reinterpret_cast<float2*>(smem + L.Hb);
+  float2* Yb = reinterpret_cast<float2*>(smem + L.Yb);
+  float2* Zb = reinterpret_cast<float2*>(smem + L.Zb);
+  float2* Zhb = reinterpret_cast<float2*>(smem + L.Zhb);
+  float2* Ub = reinterpret_cast<float2*>(smem + L.Ub);
+  float2* Pb = reinterpret_cast<float2*>(smem + L.Pb);
+  const bool stage2 = p.switch_iter >= 1 && t >= p.switch_iter;
+  const float omega = u_omega(p, t);
+  const float gam = p.gamma[t - 1];
+  const float Pc = p.P[b];
+  u_forward_iter(X, stage2, omega, Va, Vb, Vh, fail);
+  // projection: Vt = Vh - gam G, V^t = c Vt with c = sqrt(P / ||Vt||^2) when active
+  double s = 0.0, ip = 0.0;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const float2 v = make_float2(Vh[e].x - gam * X.G[e].x, Vh[e].y - gam * X.G[e].y);
+    s += (double)v.x * v.x + (double)v.y * v.y;
+    ip += (double)A1[e].x * v.x + (double)A1[e].y * v.y;
+  }
+  s = block_sum(s, red);
+  ip = block_sum(ip, red);
+  const bool active = s > (double)Pc;
+  const float cc = active ? (float)sqrt((double)Pc / s) : 1.f;
+  const float kk = active ? (float)(ip / s) : 0.f;
+  double gb = 0.0;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const float2 v = make_float2(Vh[e].x - gam * X.G[e].x, Vh[e].y - gam * X.G[e].y);
+    const float2 bt = make_float2(cc * (A1[e].x - kk * v.x), cc * (A1[e].y - kk * v.y));  // Vtilde-bar
+    B[e] = bt;
+    gb += (double)bt.x * X.G[e].x + (double)bt.y * X.G[e].y;
+  }
+  gb = block_sum(gb, red);  // also orders the writes of B before the reads below
+  if (threadIdx.x == 0) p.gamma_bar[(long long)b * p.T + (t - 1)] = (float)(-gb);
+  // Gbar = -gam B;  Ybar = H Gbar
+  u_gemm(m, n, Nt, [&](int r, int q) { return X.H[r * Nt + q]; }, [&](int q, int c) { return B[q * n + c]; },
+         [&](int r, int c, float2 v) { Yb[r * n + c] = cscale(v, -gam); });
+  __syncthreads();
+  // per user: Abar = 2 alpha P^H Ybar, Ubar, Pbar, Zhbar = U Abar; then W, E and T
+  for (int r = threadIdx.x; r < K; r += blockDim.x) {
+    const float a2 = 2.f * X.alpha[r];
+    float2 ub[16], pb[16];
+    for (int q = 0; q < Nr * d; ++q) ub[q] = pb[q] = make_float2(0.f, 0.f);
+    for (int c = 0; c < n; ++c) {
+      float2 As[kMaxNr], Ab[kMaxNr];
+      for (int s2 = 0; s2 < d; ++s2) {
+        float2 acc = make_float2(c == r * d + s2 ? -1.f : 0.f, 0.f);
+        float2 acb = make_float2(0.f, 0.f);
+        for (int a = 0; a < Nr; ++a) {
+          acc = cjfma(X.U[(r * Nr + a) * d + s2], X.Zh[(r * Nr + a) * n + c], acc);
+          acb = cjfma(X.P[(r * Nr + a) * d + s2], Yb[(r * Nr + a) * n + c], acb);
+        }
+        As[s2] = acc;
+        Ab[s2] = cscale(acb, a2);
+      }
+      for (int a = 0; a < Nr; ++a) {
+        const float2 zh = X.Zh[(r * Nr + a) * n + c], yb = Yb[(r * Nr + a) * n + c];
+        float2 zhb = make_float2(0.f, 0.f);
+        for (int s2 = 0; s2 < d; ++s2) {
+          // Ubar += Zh Abar^H;  Pbar += 2 alpha Ybar A^H;  Zhbar = U Abar
+          ub[a * d + s2] = cfma(zh, make_float2(Ab[s2].x, -Ab[s2].y), ub[a * d + s2]);
+          pb[a * d + s2] = cfma(cscale(yb, a2), make_float2(As[s2].x, -As[s2].y), pb[a * d + s2]);
+          zhb = cfma(X.U[(r * Nr + a) * d + s2], Ab[s2], zhb);
+        }
+        Zhb[(r * Nr + a) * n + c] = zhb;
+      }
+    }
+    // P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
+    Z64 Ubr[16], Wb[16], Uu[16], Wm[16], Eb[16], Bm[16], Tb[16], Ti[16];
+    for (int q = 0; q < Nr * d; ++q) Uu[q] = zld(X.U[r * Nr * d + q]);
+    for (int q = 0; q < d * d; ++q) Wm[q] = zld(X.W[r * d * d + q]);
+    for (int q = 0; q < Nr * Nr; ++q) Ti[q] = zld(X.Ti[r * Nr * Nr + q]);
+    for (int a = 0; a < Nr; ++a)
+      for (int s2 = 0; s2 < d; ++s2) {
+        Z64 acc = zld(ub[a * d + s2]);
+        for (int u = 0; u < d; ++u) acc = zadd(acc, zmul(zld(pb[a * d + u]), zmk(Wm[s2 * d + u].x, -Wm[s2 * d + u].y)));
+        Ubr[a * d + s2] = acc;
+      }
+    for (int q = 0; q < d * d; ++q) Eb[q] = zmk(0.0, 0.0);
+    if (stage2) {
+      for (int s2 = 0; s2 < d; ++s2)
+        for (int u = 0; u < d; ++u) {
+          Z64 acc = zmk(0.0, 0.0);
+          for (int a = 0; a < Nr; ++a) acc = zadd(acc, zcmul(Uu[a * d + s2], zld(pb[a * d + u])));
+          Wb[s2 * d + u] = acc;
+        }
+      // W = E^{-1}: Ebar = -W^H Wbar W^H  (W Hermitian)
+      Z64 tmp[16];
+      for (int s2 = 0; s2 < d; ++s2)
+        for (int u = 0; u < d; ++u) {
+          Z64 acc = zmk(0.0, 0.0);
+          for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(Wm[s2 * d + v], Wb[v * d + u]));
+          tmp[s2 * d + u] = acc;
+        }
+      for (int s2 = 0; s2 < d; ++s2)
+        for (int u = 0; u < d; ++u) {
+          Z64 acc = zmk(0.0, 0.0);
+          for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(tmp[s2 * d + v], Wm[v * d + u]));
+          Eb[s2 * d + u] = zmk(-acc.x, -acc.y);
+        }
+      // E = I - U^H Zo: Ubar += -Zo Ebar^H
+      for (int a = 0; a < Nr; ++a)
+        for (int s2 = 0; s2 < d; ++s2) {
+          Z64 acc = Ubr[a * d + s2];
+          for (int u = 0; u < d; ++u) {
+            const Z64 zo = zld(X.Z[(r * Nr + a) * n + r * d + u]);
+            acc = zsub(acc, zmul(zo, zmk(Eb[s2 * d + u].x, -Eb[s2 * d + u].y)));
+          }
+          Ubr[a * d + s2] = acc;
+        }
+    }
+    // U = T^{-1} Zo: Bm = T^{-1} Ubar; Zo-bar += Bm; Tbar = -Bm U^H
+    for (int a = 0; a < Nr; ++a)
+      for (int s2 = 0; s2 < d; ++s2) {
+        Z64 acc = zmk(0.0, 0.0);
+        for (int c2 = 0; c2 < Nr; ++c2) acc = zadd(acc, zmul(Ti[a * Nr + c2], Ubr[c2 * d + s2]));
+        Bm[a * d + s2] = acc;
+      }
+    for (int a = 0; a < Nr; ++a)
+      for (int c2 = 0; c2 < Nr; ++c2) {
+        Z64 acc = zmk(0.0, 0.0);
+        for (int s2 = 0; s2 < d; ++s2) acc = zsub(acc, zmul(Bm[a * d + s2], zmk(Uu[c2 * d + s2].x, -Uu[c2 * d + s2].y)));
+        Tb[a * Nr + c2] = acc;
+      }
+    // T = I + Z Z^H: Zbar_r = (Tbar + Tbar^H) Z_r; own columns also get Bm - U Ebar
+    for (int c = 0; c < n; ++c) {
+      const bool own = c >= r * d && c < r * d + d;
+      for (int a = 0; a < Nr; ++a) {
+        Z64 acc = zmk(0.0, 0.0);
+        for (int c2 = 0; c2 < Nr; ++c2) {
+          const Z64 sym = zmk(Tb[a * Nr + c2].x + Tb[c2 * Nr + a].x, Tb[a * Nr + c2].y - Tb[c2 * Nr + a].y);
+          acc = zadd(acc, zmul(sym, zld(X.Z[(r * Nr + c2) * n + c])));
+        }
+        if (own) {
+          const int s2 = c - r * d;
+          acc = zadd(acc, Bm[a * d + s2]);
+          for (int u = 0; u < d; ++u) acc = zsub(acc, zmul(Uu[a * d + u], Eb[u * d + s2]));
+        }
+        Zb[(r * Nr + a) * n + c] = zst(acc);
+      }
+    }
+    for (int q = 0; q < Nr * d; ++q) {
+      Ub[r * Nr * d + q] = zst(Ubr[q]);
+      Pb[r * Nr * d + q] = pb[q];
+    }
+  }
+  __syncthreads();
+  // Hbar += Y Gbar^H + Zhbar Vhat^H + Zbar Va^H  (Gbar = -gam B)
+  for (int e = threadIdx.x; e < m * Nt; e += blockDim.x) {
+    const int i = e / Nt, q = e - i * Nt;
+    float2 acc = Hb[e];
+    for (int c = 0; c < n; ++c) {
+      const float2 gbar = cscale(B[q * n + c], -gam);
+      acc = cfma(X.Y[i * n + c], make_float2(gbar.x, -gbar.y), acc);
+      acc = cfma(Zhb[i * n + c], make_float2(Vh[q * n + c].x, -Vh[q * n + c].y), acc);
+      acc = cfma(Zb[i * n + c], make_float2(Va[q * n + c].x, -Va[q * n + c].y), acc);
+    }
+    Hb[e] = acc;
+  }
+  __syncthreads();
+  // Vhat-bar = B + H^H Zhbar (in B);  A2 += H^H Zbar + (1 + w) Vhat-bar;  A3 = -w Vhat-bar
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int q = e / n, c = e - q * n;
+    float2 vhb = B[e], zz = make_float2(0.f, 0.f);
+    for (int i = 0; i < m; ++i) {
+      const float2 hc = make_float2(X.H[i * Nt + q].x, -X.H[i * Nt + q].y);
+      vhb = cfma(hc, Zhb[i * n + c], vhb);
+      zz = cfma(hc, Zb[i * n + c], zz);
+    }
+    A2[e] = make_float2(A2[e].x + zz.x + (1.f + omega) * vhb.x, A2[e].y + zz.y + (1.f + omega) * vhb.y);
+    A3[e] = make_float2(-omega * vhb.x, -omega * vhb.y);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kUThreads) u_backward_kernel(UParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_fail;
+  const int b = blockIdx.x;
+  const ULayout L = u_layout(p.K, p.Nt, p.Nr, p.d);
+  const UView X = u_view(p, smem, L, b);
+  if (threadIdx.x == 0) s_fail = kOk;
+  const int N = X.Nt * X.n;
+  u_load_h(p, X, b);
+  float2* Vh = reinterpret_cast<float2*>(smem + L.Vh);
+  float2* Va = reinterpret_cast<float2*>(smem + L.Va);
+  float2* Vb = reinterpret_cast<float2*>(smem + L.Vb);
+  float2* Acc[3] = {reinterpret_cast<float2*>(smem + L.A1), reinterpret_cast<float2*>(smem + L.A2),
+                    reinterpret_cast<float2*>(smem + L.A3)};
+  float2* Hb = reinterpret_cast<float2*>(smem + L.Hb);
+  double* red = reinterpret_cast<double*>(smem + L.red);
+  const double wb = p.wsr_bar[b] / 0.69314718055994530942;  // dL / dWSR in nats
+  // WSR(V^T): Vbar^T = -wb G*, Hbar = -wb Y* (V^T)^H at the MMSE receiver and W = E^{-1}
+  const float2* cT = u_ckpt(p, b, 2 * p.nseg);
+  for (int e = threadIdx.x; e < N; e += blockDim.x) Va[e] = cT[e];
+  __syncthreads();
+  u_forward_iter(X, true, 0.f, Va, Va, Vh, &s_fail);
+  const float wf = (float)wb;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    Acc[0][e] = cscale(X.G[e], -wf);
+    Acc[1][e] = make_float2(0.f, 0.f);
+  }
+  for (int e = threadIdx.x; e < X.m * X.Nt; e += blockDim.x) {
+    const int i = e / X.Nt, q = e - i * X.Nt;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c = 0; c < X.n; ++c) acc = cfma(X.Y[i * X.n + c], make_float2(Va[q * X.n + c].x, -Va[q * X.n + c].y), acc);
+    Hb[e] = cscale(acc, -wf);
+  }
+  __syncthreads();
+  const long long vn = (long long)N;
+  float2* hist = p.hist + (long long)b * (p.ck + 2) * vn;  // hist[j] = V^{c0 - 1 + j}
+  for (int sg = p.nseg - 1; sg >= 0; --sg) {
+    const int c0 = sg * p.ck, c1 = min(c0 + p.ck, p.T);
+    const float2* k0 = u_ckpt(p, b, 2 * sg);
+    const float2* k1 = u_ckpt(p, b, 2 * sg + 1);
+    for (int e = threadIdx.x; e < N; e += blockDim.x) {
+      Vb[e] = hist[e] = k0[e];
+      Va[e] = hist[vn + e] = k1[e];
+    }
+    __syncthreads();
+    // recompute V^{c0+1} .. V^{c1-1} into hist
+    for (int t = c0 + 1; t < c1; ++t) {
+      const bool stage2 = p.switch_iter >= 1 && t >= p.switch_iter;
+      u_forward_iter(X, stage2, u_omega(p, t), Va, Vb, Vh, &s_fail);
+      float2* dst = hist + (long long)(t - c0 + 1) * vn;
+      u_step_project(X, p.gamma[t - 1], p.P[b], Vh, Vb, red);  // V^t into Vb
+      for (int e = threadIdx.x; e < N; e += blockDim.x) dst[e] = Vb[e];
+      float2* tmp = Va;
+      Va = Vb;
+      Vb = tmp;
+      __syncthreads();
+    }
+    for (int t = c1; t > c0; --t) {
+      const float2* hVa = hist + (long long)(t - c0) * vn;      // V^{t-1}
+      const float2* hVb = hist + (long long)(t - c0 - 1) * vn;  // V^{t-2}
+      for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        Va[e] = hVa[e];
+        Vb[e] = hVb[e];
+      }
+      __syncthreads();
+      u_adjoint_iter(p, X, L, smem, b, t, Va, Vb, Acc[0], Acc[1], Acc[2], &s_fail);
+      float2* t0 = Acc[0];
+      Acc[0] = Acc[1];
+      Acc[1] = Acc[2];
+      Acc[2] = t0;
+    }
+  }
+  // Hbar for the channels as given: H_n = H / sigma_r
+  float2* Hg = p.H_bar + (long long)b * X.m * X.Nt;
+  for (int e = threadIdx.x; e < X.m * X.Nt; e += blockDim.x) {
+    const int i = e / X.Nt;
+    Hg[e] = cscale(Hb[e], rsqrtf(p.sigma2[(long long)b * X.K + i / X.Nr]));
+  }
+  if (threadIdx.x == 0 && s_fail != kOk) p.status[b] = s_fail;
+}
+
+}  // namespace
+}  // namespace amm
+
+struct amm_unrolled {
+  int batch = 0, K = 0, Nt = 0, Nr = 0, d = 0, T = 0, ck = 0, nseg = 0, switch_iter = 0, extrapolate = 1;
+  int smem = 0;
+  cudaStream_t stream = nullptr;
+  float2* ckpt = nullptr;
+  float2* hist = nullptr;
+  int* status = nullptr;
+  const void* H = nullptr;
+  const float *sigma2 = nullptr, *alpha = nullptr, *P = nullptr, *gamma = nullptr;
+  bool forward_done = false;
+  std::string err;
+};
+
+static thread_local std::string g_unrolled_err;
+
+static amm_status u_fail(amm_unrolled* u, amm_status s, const std::string& msg) {
+  if (u) u->err = msg;
+  g_unrolled_err = msg;
+  return s;
+}
+
+extern "C" amm_status amm_unrolled_create(amm_unrolled** out, int batch, const amm_dims* dims, int T, int ckpt_every,
+                                          int switch_iter, int extrapolate, void* stream) {
+  if (!out || !dims || batch < 1 || T < 1 || ckpt_every < 1)
+    return u_fail(nullptr, AMM_EINVAL, "amm_unrolled_create: null pointer, batch < 1, T < 1 or ckpt_every < 1");
+  *out = nullptr;
+  const amm_dims& D = *dims;
+  if (D.cells != 1) return u_fail(nullptr, AMM_EUNSUPPORTED, "amm_unrolled_create: one cell per instance only");
+  if (D.users < 1 || D.nt < 1 || D.nr < 1 || D.nr > amm::kMaxNr || D.d < 1 || D.d > D.nr)
+    return u_fail(nullptr, AMM_EINVAL, "amm_unrolled_create: dims out of range (1 <= d <= nr <= 4)");
+  const amm::ULayout L = amm::u_layout(D.users, D.nt, D.nr, D.d);
+  if (L.total > amm::kSmemMax - 1024)
+    return u_fail(nullptr, AMM_EUNSUPPORTED, "amm_unrolled_create: instance too large for shared memory");
+  amm_unrolled* u = new (std::nothrow) amm_unrolled();
+  if (!u) return u_fail(nullptr, AMM_ENOMEM, "amm_unrolled_create: out of host memory");
+  u->batch = batch;
+  u->K = D.users;
+  u->Nt = D.nt;
+  u->Nr = D.nr;
+  u->d = D.d;
+  u->T = T;
+  u->ck = ckpt_every;
+  u->nseg = (T + ckpt_every - 1) / ckpt_every;
+  u->switch_iter = switch_iter;
+  u->extrapolate = extrapolate ? 1 : 0;
+  u->smem = L.total;
+  u->stream = static_cast<cudaStream_t>(stream);
+  const long long vn = (long long)D.nt * D.users * D.d;
+  cudaError_t e;
+  if ((e = cudaMalloc(&u->ckpt, sizeof(float2) * vn * (2 * u->nseg + 1) * batch)) ||
+      (e = cudaMalloc(&u->hist, sizeof(float2) * vn * (u->ck + 2) * batch)) ||
+      (e = cudaMalloc(&u->status, sizeof(int) * batch)) ||
+      (e = cudaFuncSetAttribute(amm::u_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total)) ||
+      (e = cudaFuncSetAttribute(amm::u_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total))) {
+    std::string msg = std::string("amm_unrolled_create: ") + cudaGetErrorString(e);
+    cudaFree(u->ckpt);
+    cudaFree(u->hist);
+    cudaFree(u->status);
+    delete u;
+    return u_fail(nullptr, e == cudaErrorMemoryAllocation ? AMM_ENOMEM : AMM_ECUDA, msg);
+  }
+  *out = u;
+  return AMM_OK;
+}
+
+static amm::UParams u_params(amm_unrolled* u) {
+  amm::UParams p;
+  memset(&p, 0, sizeof p);
+  p.batch = u->batch;
+  p.K = u->K;
+  p.Nt = u->Nt;
+  p.Nr = u->Nr;
+  p.d = u->d;
+  p.T = u->T;
+  p.ck = u->ck;
+  p.nseg = u->nseg;
+  p.switch_iter = u->switch_iter;
+  p.extrapolate = u->extrapolate;
+  p.H = static_cast<const float2*>(u->H);
+  p.sigma2 = u->sigma2;
+  p.alpha = u->alpha;
+  p.P = u->P;
+  p.gamma = u->gamma;
+  p.ckpt = u->ckpt;
+  p.hist = u->hist;
+  p.status = u->status;
+  return p;
+}
+
+extern "C" amm_status amm_unrolled_forward(amm_unrolled* u, const void* H, const float* alpha, const float* sigma2,
+                                           const float* P, const void* V0, const float* gamma, double* wsr) {
+  if (!u) return AMM_EINVAL;
+  if (!H || !alpha || !sigma2 || !P || !V0 || !gamma || !wsr)
+    return u_fail(u, AMM_EINVAL, "amm_unrolled_forward: every pointer is required");
+  u->H = H;
+  u->alpha = alpha;
+  u->sigma2 = sigma2;
+  u->P = P;
+  u->gamma = gamma;
+  amm::UParams p = u_params(u);
+  p.V0 = static_cast<const float2*>(V0);
+  p.wsr = wsr;
+  amm::u_forward_kernel<<<u->batch, amm::kUThreads, u->smem, u->stream>>>(p);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return u_fail(u, AMM_ECUDA, std::string("amm_unrolled_forward: ") + cudaGetErrorString(e));
+  u->forward_done = true;
+  return AMM_OK;
+}
+
+extern "C" amm_status amm_unrolled_backward(amm_unrolled* u, const double* wsr_bar, float* gamma_bar, void* H_bar) {
+  if (!u) return AMM_EINVAL;
+  if (!wsr_bar || !gamma_bar || !H_bar) return u_fail(u, AMM_EINVAL, "amm_unrolled_backward: every pointer is required");
+  if (!u->forward_done) return u_fail(u, AMM_EINVAL, "amm_unrolled_backward before amm_unrolled_forward");
+  amm::UParams p = u_params(u);
+  p.wsr_bar = wsr_bar;
+  p.gamma_bar = gamma_bar;
+  p.H_bar = static_cast<float2*>(H_bar);
+  amm::u_backward_kernel<<<u->batch, amm::kUThreads, u->smem, u->stream>>>(p);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return u_fail(u, AMM_ECUDA, std::string("amm_unrolled_backward: ") + cudaGetErrorString(e));
+  return AMM_OK;
+}
+
+extern "C" amm_status amm_unrolled_status(amm_unrolled* u, int* status_dev) {
+  if (!u || !status_dev) return AMM_EINVAL;
+  const cudaError_t e =
+      cudaMemcpyAsync(status_dev, u->status, sizeof(int) * u->batch, cudaMemcpyDeviceToDevice, u->stream);
+  return e == cudaSuccess ? AMM_OK : u_fail(u, AMM_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" const char* amm_unrolled_last_error(amm_unrolled* u) {
+  return u ? u->err.c_str() : g_unrolled_err.c_str();
+}
+
+extern "C" void amm_unrolled_destroy(amm_unrolled* u) {
+  if (!u) return;
+  cudaFree(u->ckpt);
+  cudaFree(u->hist);
+  cudaFree(u->status);
+  delete u;
+}

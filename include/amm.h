@@ -104,13 +104,16 @@ typedef struct {
   int fp64_solves;      /* 1: the per-user Nr x Nr / d x d Cholesky solves of the U
                            and W updates run in FP64 (default); 0: in FP32.  The
                            WSR evaluation of amm_wsr is FP64 either way. */
+  int gemm_tile;        /* register tile of the FP32-path block GEMMs: 0 automatic
+                           (by instance size), 1: 4x4, 2: 2x2, 3: 4x2 (set by
+                           the autotuner); 0 */
 } amm_opts;
 
 typedef struct amm_ctx amm_ctx;
 
 /* Fill *opts with the defaults: eps1 0.1, eps2 1e-3, tc 3, gamma_c 0,
  * extrapolate 1, switch_iter -1, step_rule 0, AMM_FP32, u_at_extrapolated 0,
- * lanczos_steps 64, spin_budget 2e9, smem_budget 0, fp64_solves 1. */
+ * lanczos_steps 64, spin_budget 2e9, smem_budget 0, fp64_solves 1, gemm_tile 0. */
 AMM_API void amm_default_opts(amm_opts* opts);
 
 /* Create a solver for `batch` instances.  `dims` points to `n_dims` entries:
@@ -246,6 +249,33 @@ AMM_API const char* amm_last_error(const amm_ctx* ctx);
 
 /* Number of kernel launches this context has issued, for launch accounting. */
 AMM_API int64_t amm_launch_count(const amm_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * CUDA graph of a whole solve.
+ *
+ * amm_graph_create records, on a private capture stream, what
+ * amm_set_problem(H, alpha, sigma2, P) + amm_warmstart(V0) +
+ * amm_step(n_iters) + amm_wsr(wsr) enqueue (the normalisation, the warm
+ * start, one persistent launch that runs all n_iters iterations of
+ * Algorithm 3, and the FP64 WSR), and instantiates it.  amm_graph_launch
+ * replays it on the context's stream: one graph launch per solve, reading
+ * the inputs from the same caller buffers each time, so a caller refills
+ * H / alpha / sigma2 / P / V0 in place between replays (stream-ordered) and
+ * replays.  The graph belongs to ctx and uses its workspace: do not destroy
+ * ctx before the graph, and do not interleave other ctx calls with a replay
+ * in flight.  (The paper has no counterpart: a serving entry point.)
+ * ------------------------------------------------------------------- */
+typedef struct amm_graph amm_graph;
+
+AMM_API amm_status amm_graph_create(amm_ctx* ctx, const void* H, const float* alpha, const float* sigma2,
+                                    const float* P, const void* V0, int n_iters, double* wsr,
+                                    amm_graph** out);
+
+/* Replay the recorded solve on the context's stream (asynchronous). */
+AMM_API amm_status amm_graph_launch(amm_graph* g);
+
+/* Release the graph (its context stays). */
+AMM_API void amm_graph_destroy(amm_graph* g);
 
 /* ---------------------------------------------------------------------
  * Differentiable unrolled A-MMMSE.

@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
                 ("gamma_c", ctypes.c_double), ("extrapolate", ctypes.c_int), ("switch_iter", ctypes.c_int),
                 ("step_rule", ctypes.c_int), ("precision", ctypes.c_int), ("u_at_extrapolated", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
-                ("smem_budget", ctypes.c_int), ("fp64_solves", ctypes.c_int)]
+                ("smem_budget", ctypes.c_int), ("fp64_solves", ctypes.c_int), ("gemm_tile", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -48,7 +48,7 @@ class State(ctypes.Structure):
 EXPORTS = ["amm_default_opts", "amm_create", "amm_sizes", "amm_set_problem", "amm_warmstart", "amm_step",
            "amm_solve", "amm_wsr", "amm_wmmse_step", "amm_get_V", "amm_get_state", "amm_set_state",
            "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count",
-           "amm_solve_noalloc", "amm_unrolled_create", "amm_unrolled_forward", "amm_unrolled_backward",
+           "amm_solve_noalloc", "amm_graph_create", "amm_graph_launch", "amm_graph_destroy", "amm_unrolled_create", "amm_unrolled_forward", "amm_unrolled_backward",
            "amm_unrolled_status", "amm_unrolled_last_error", "amm_unrolled_destroy"]
 
 _lib = None
@@ -85,6 +85,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "amm_launch_count": (i64, [vp]),
         "amm_solve_noalloc": (i32, [i32, ctypes.POINTER(Dims), ctypes.POINTER(Opts), vp, vp, vp, vp, vp, i32, vp,
                                     vp, vp, ctypes.c_char_p, i32]),
+        "amm_graph_create": (i32, [vp, vp, vp, vp, vp, vp, i32, vp, ctypes.POINTER(vp)]),
+        "amm_graph_launch": (i32, [vp]),
+        "amm_graph_destroy": (None, [vp]),
         "amm_unrolled_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(Dims), i32, i32, i32, i32, vp]),
         "amm_unrolled_forward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "amm_unrolled_backward": (i32, [vp, vp, vp, vp]),
@@ -244,6 +247,35 @@ class Solver:
     @property
     def launches(self) -> int:
         return int(self.lib.amm_launch_count(self.h))
+
+    def capture(self, H, alpha, sigma2, P, V0, n_iters: int, wsr_out) -> "Graph":
+        """Record set_problem + warmstart + step(n_iters) + wsr as a CUDA graph
+        (amm_graph_create); Graph.launch() replays it."""
+        g = ctypes.c_void_p()
+        self._check(self.lib.amm_graph_create(self.h, _ptr(H), _ptr(alpha), _ptr(sigma2), _ptr(P), _ptr(V0),
+                                              n_iters, _ptr(wsr_out), ctypes.byref(g)))
+        return Graph(self, g, (H, alpha, sigma2, P, V0, wsr_out))
+
+
+class Graph:
+    """A recorded solve of one Solver (amm_graph_*)."""
+
+    def __init__(self, solver: Solver, handle, keep):
+        self.solver, self.h, self._keep = solver, handle, keep
+
+    def launch(self):
+        self.solver._check(self.solver.lib.amm_graph_launch(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.solver.lib.amm_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class UnrolledSolver:

@@ -178,6 +178,7 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
     return fail(nullptr, AMM_EINVAL, "a fixed step needs gamma_c > 0");
   if (o.lanczos_steps < 1 || o.lanczos_steps > amm::kMaxLanczos)
     return fail(nullptr, AMM_EINVAL, "lanczos_steps must be in [1, 64]");
+  if (o.gemm_tile < 0 || o.gemm_tile > 3) return fail(nullptr, AMM_EINVAL, "gemm_tile must be in [0, 3]");
   if (o.spin_budget < 1) o.spin_budget = 2000000000ll;
 
   amm_ctx* c = new (std::nothrow) amm_ctx();
@@ -345,6 +346,7 @@ static amm::IterParams base_params(amm_ctx* c) {
   p.switch_iter = c->opts.switch_iter;
   p.step_rule = c->opts.step_rule;
   p.lanczos_steps = c->opts.lanczos_steps;
+  p.gemm_tile = c->opts.gemm_tile;
   p.smem_budget = c->smem_budget;
   p.spin_budget = c->opts.spin_budget;
   return p;
@@ -510,3 +512,72 @@ extern "C" const char* amm_last_error(const amm_ctx* c) {
 }
 
 extern "C" int64_t amm_launch_count(const amm_ctx* c) { return c ? c->launches : 0; }
+
+// ---------------------------------------------------------------- CUDA graph
+struct amm_graph {
+  amm_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;  // kernel launches one replay issues
+};
+
+extern "C" amm_status amm_graph_create(amm_ctx* c, const void* H, const float* alpha, const float* sigma2,
+                                       const float* P, const void* V0, int n_iters, double* wsr,
+                                       amm_graph** out) {
+  if (!c) return AMM_EINVAL;
+  if (!out || !H || !alpha || !sigma2 || !P || !V0 || !wsr || n_iters < 1)
+    return fail(c, AMM_EINVAL, "amm_graph_create: null pointer or n_iters < 1");
+  *out = nullptr;
+  amm_graph* g = new (std::nothrow) amm_graph();
+  if (!g) return fail(c, AMM_ENOMEM, "amm_graph_create: out of host memory");
+  g->ctx = c;
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(c, e, "amm_graph_create: capture stream");
+  }
+  const cudaStream_t saved = c->stream;
+  const int64_t before = c->launches;
+  c->stream = cap;
+  amm_status s = AMM_OK;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    s = amm_set_problem(c, H, alpha, sigma2, P);
+    if (s == AMM_OK) s = amm_warmstart(c, V0);
+    if (s == AMM_OK) s = amm_step(c, n_iters);
+    if (s == AMM_OK) s = amm_wsr(c, wsr);
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &g->graph);
+    if (s == AMM_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "amm_graph_create: end capture");
+  } else {
+    s = cuda_fail(c, e, "amm_graph_create: begin capture");
+  }
+  c->stream = saved;
+  cudaStreamDestroy(cap);
+  g->launches = c->launches - before;
+  c->launches = before;  // recorded, not launched
+  if (s == AMM_OK && (e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess)
+    s = cuda_fail(c, e, "amm_graph_create: instantiate");
+  if (s != AMM_OK) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return s;
+  }
+  *out = g;
+  return AMM_OK;
+}
+
+extern "C" amm_status amm_graph_launch(amm_graph* g) {
+  if (!g) return AMM_EINVAL;
+  const cudaError_t e = cudaGraphLaunch(g->exec, g->ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(g->ctx, e, "amm_graph_launch");
+  g->ctx->launches += g->launches;
+  return AMM_OK;
+}
+
+extern "C" void amm_graph_destroy(amm_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}

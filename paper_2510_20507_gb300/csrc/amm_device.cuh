@@ -65,6 +65,29 @@ __device__ __forceinline__ void block_cgemm(int M, int N, int KK, const float2* 
   }
 }
 
+// Register tile of the plain-path block GEMMs: 1 = 4 x 4, 2 = 2 x 2,
+// 3 = 4 x 2; 0 picks the largest tile that still gives every thread of the
+// block at least one tile (small instances leave most threads idle with
+// 4 x 4 tiles).
+__device__ __forceinline__ int gemm_tile_for(int opt, int M, int N) {
+  if (opt >= 1 && opt <= 3) return opt;
+  const int nb = (int)blockDim.x;
+  if (((M + 3) / 4) * ((N + 3) / 4) >= nb) return 1;
+  if (((M + 3) / 4) * ((N + 1) / 2) >= nb) return 3;
+  return 2;
+}
+
+template <int OPA, class Epi>
+__device__ __forceinline__ void block_cgemm_tiled(int tile, int M, int N, int KK, const float2* __restrict__ A,
+                                                  int lda, const float2* __restrict__ B, int ldb, Epi epi) {
+  if (tile == 2)
+    block_cgemm<2, 2, OPA>(M, N, KK, A, lda, B, ldb, epi);
+  else if (tile == 3)
+    block_cgemm<4, 2, OPA>(M, N, KK, A, lda, B, ldb, epi);
+  else
+    block_cgemm<4, 4, OPA>(M, N, KK, A, lda, B, ldb, epi);
+}
+
 // ------------------------------------------------------- bulk staging
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));

@@ -60,7 +60,7 @@ struct IterParams {
   int n_iters;
   int mode;
   float eps1, eps2, gamma_user;
-  int tc, extrapolate, switch_iter, step_rule, lanczos_steps;
+  int tc, extrapolate, switch_iter, step_rule, lanczos_steps, gemm_tile;
   int smem_budget;
   long long spin_budget;
 };

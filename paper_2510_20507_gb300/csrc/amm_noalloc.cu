@@ -98,7 +98,7 @@ extern "C" amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const a
     return noalloc_fail(err, err_len, AMM_EINVAL, "amm_solve_noalloc: only the FP32 GEMM path (AMM_FP32)");
   if (o.u_at_extrapolated || o.step_rule < 0 || o.step_rule > 2 || o.tc < 0 ||
       ((o.step_rule == 2 || (o.step_rule == 0 && o.tc == 0)) && !(o.gamma_c > 0)) || o.lanczos_steps < 1 ||
-      o.lanczos_steps > kMaxLanczos)
+      o.lanczos_steps > kMaxLanczos || o.gemm_tile < 0 || o.gemm_tile > 3)
     return noalloc_fail(err, err_len, AMM_EINVAL, "amm_solve_noalloc: unsupported option combination");
   const amm_dims& d = dims[0];
   if (d.cells < 1 || d.cells > kMaxCells || d.users < 1 || d.nt < 1 || d.nt > 4096 || d.nr < 1 ||
@@ -190,6 +190,7 @@ extern "C" amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const a
   p.switch_iter = o.switch_iter;
   p.step_rule = o.step_rule;
   p.lanczos_steps = o.lanczos_steps;
+  p.gemm_tile = o.gemm_tile;
   p.smem_budget = budget;
   p.spin_budget = o.spin_budget > 0 ? o.spin_budget : 2000000000ll;
   if (n_iters > 0) {

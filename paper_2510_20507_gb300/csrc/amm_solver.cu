@@ -133,12 +133,13 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   int cur = 0;  // V[cur] = V^{t-1}, V[cur^1] = V^{t-2}; Z[zc] = Z(V^{t-1}), Z[zc^1] = Z(V^{t-2})
   int zc = 0;
   const int ldh = vw.ldh, ldv = vw.ldv, ldz = vw.ldz;
+  const int tile_z = gemm_tile_for(p.gemm_tile, m, n), tile_g = gemm_tile_for(p.gemm_tile, Nt, n);
 
   // Z(V^{t-2}) is needed from t = 3 on (omega > 0); rebuild it once per launch.
   if (p.mode != kEvalWsr && p.extrapolate && s_ctrl[0] >= 3) {
     for (int j = 0; j < C; ++j) {
       float2* Zo = vw.Z[zc ^ 1] + j * n;
-      block_cgemm<4, 4, 0>(m, n, Nt, vw.H + (long long)j * m * ldh, ldh, vw.V[cur ^ 1] + (long long)j * Nt * ldv,
+      block_cgemm_tiled<0>(tile_z, m, n, Nt, vw.H + (long long)j * m * ldh, ldh, vw.V[cur ^ 1] + (long long)j * Nt * ldv,
                            ldv, [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
     }
     __syncthreads();
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     // ---- S2: Z = H V^{t-1}
     for (int j = 0; j < C; ++j) {
       float2* Zo = Zc + j * n;
-      block_cgemm<4, 4, 0>(m, n, Nt, vw.H + (long long)j * m * ldh, ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
+      block_cgemm_tiled<0>(tile_z, m, n, Nt, vw.H + (long long)j * m * ldh, ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
                            [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
     }
     __syncthreads();
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
       const float2* Vc = vw.V[cur] + (long long)j * Nt * ldv;
       float2* Vn = vw.V[cur ^ 1] + (long long)j * Nt * ldv;
       float nrm = 0.f;
-      block_cgemm<4, 4, 1>(Nt, n, m, vw.H + (long long)j * m * ldh, ldh, Zp + j * n, ldz,
+      block_cgemm_tiled<1>(tile_g, Nt, n, m, vw.H + (long long)j * m * ldh, ldh, Zp + j * n, ldz,
                            [&](int r, int c, float2 g) {
                              const long long idx = (long long)r * ldv + c;
                              float2 vh = Vc[idx];

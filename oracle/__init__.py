@@ -10,4 +10,4 @@ perturbation and finite-difference checks, the paper's lemmas).  The WSR
 values in the paper's figures are not printed in its text, so the match
 with the paper's own numbers is parity unpinned.
 """
-from . import model, solvers, closed_forms  # noqa: F401
+from . import model, solvers, closed_forms, sensitivity  # noqa: F401

@@ -116,36 +116,11 @@ def oracle_wsr_bits(inst, V):
 SENSITIVE = 1e-5
 
 
-def _perturbed_wsr(inst, iters, cov32, v32, step_rel):
-    exact_cov, exact_step = om.receive_covariance, om.spectral_step
-    if cov32:
-        om.receive_covariance = lambda *a: exact_cov(*a).astype(np.complex64).astype(np.complex128)
-    if step_rel:
-        om.spectral_step = lambda *a: exact_step(*a) * (1 + step_rel)
-    try:
-        V0 = osv.initial_precoder(inst.G0, inst.P)
-        st = osv.AState(V=V0.copy(), Vprev=V0.copy())
-        for _ in range(iters):
-            osv.ammmse_iteration(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, st,
-                                 osv.Options())
-            if v32:
-                st.V = st.V.astype(np.complex64).astype(np.complex128)
-        return oracle_wsr_bits(inst, st.V)
-    finally:
-        om.receive_covariance, om.spectral_step = exact_cov, exact_step
-
-
 def oracle_fp32_spread(inst, iters):
-    """Largest relative change of the oracle's final WSR under FP32-sized
-    perturbations of its otherwise FP64 arithmetic: the N_r x N_r receive
-    covariance of eq. (9) stored in complex64, the iterate V stored in
-    complex64 after every iteration, the spectral step of eq. (16) off by
-    5e-7 relative (the accuracy of an FP32 Lanczos estimate of ||F_k||_2),
-    and all three together.  Single perturbations can cancel by chance on a
-    sensitive instance; the largest of the four is the estimate."""
-    ref = oracle_wsr_bits(inst, oracle_run(inst, iters).V)
-    variants = [(True, False, 0.0), (False, True, 0.0), (False, False, -5e-7), (True, True, 5e-7)]
-    return max(abs(_perturbed_wsr(inst, iters, *v) - ref) / ref for v in variants)
+    """oracle.sensitivity.fp32_spread: the largest relative change of the
+    oracle's final WSR under FP32-sized perturbations of its arithmetic."""
+    from oracle.sensitivity import fp32_spread
+    return fp32_spread(inst, iters)
 
 
 def check_free_running(got, insts, iters, label, sample=None, tol=1e-3):

@@ -549,14 +549,16 @@ static __device__ __noinline__ bool small_solve_pair_dispatch(int Nr, int d, int
 // ------------------------------------------------------- Lanczos ||F_k||_2
 // Number of eigenvalues of the symmetric tridiagonal T (diagonal a,
 // off-diagonal b, order n) below x: the negative pivots of T - x I (Sturm
-// count, FP32, tiny pivots pushed to the negative side).
+// count, FP32, tiny pivots pushed to the negative side).  Only the signs of
+// the pivots matter and the recurrence is backward stable, so the division
+// is the fast approximate one (a few ulp), which shortens the serial chain.
 static __device__ __forceinline__ int sturm_below(const float* a, const float* b, int n, float x, float scale) {
   int below = 0;
   float q = a[0] - x;
   if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
   below += q < 0.f;
   for (int i = 1; i < n; ++i) {
-    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+    q = (a[i] - x) - __fdividef(b[i - 1] * b[i - 1], q);
     if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
     below += q < 0.f;
   }
@@ -872,7 +874,7 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
 }
 
 // S6: Y_r = 2 alpha_r P_r (U_r^H zhat_r - S_r) for every user r and stream
-// column c; sink(row, c, value) receives Y[row][c] for the Nr rows of r.
+// column c; sink(r, c, y) receives y[a] = Y[r Nr + a][c] for the Nr rows of r.
 template <class ZGet, class Sink>
 __device__ __forceinline__ void gradient_rhs_phase(const InstDesc& D, const Layout& Ly, ZGet zhat,
                                                    const float2* sU, const float2* sP, const float* alpha_u,
@@ -899,16 +901,18 @@ __device__ __forceinline__ void gradient_rhs_phase(const InstDesc& D, const Layo
       }
     }
     const float sc2 = 2.f * alpha_u[r];
+    float2 y[kMaxNr];
 #pragma unroll
     for (int a = 0; a < kMaxNr; ++a) {
+      float2 acc = make_float2(0.f, 0.f);
       if (a < Nr) {
-        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int s = 0; s < kMaxNr; ++s)
           if (s < d) acc = cfma(Pr[a * d + s], ts[s], acc);
-        sink(r * Nr + a, c, cscale(acc, sc2));
       }
+      y[a] = cscale(acc, sc2);
     }
+    sink(r, c, y);
   }
 }
 

@@ -187,7 +187,9 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
           if (omega != 0.f) v = csub(cscale(v, 1.f + omega), cscale(Zp[idx], omega));
           return v;
         },
-        sU, sP, alpha_u, [&](int row, int c, float2 y) { Zp[(long long)row * ldz + c] = y; });
+        sU, sP, alpha_u, [&](int r, int c, const float2* y) {
+          for (int a = 0; a < D.Nr; ++a) Zp[(long long)(r * D.Nr + a) * ldz + c] = y[a];
+        });
     __syncthreads();
     // ---- S5: step size per cell, eq. (16)
     const int sflag = s_ctrl[6];

@@ -170,6 +170,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     }
     if (NS > 2) t[2] = __float2bfloat16_rn(r);
   };
+  auto pack_bf16x2 = [](__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+  };
   auto put = [&](unsigned char* const* Ar, int row, int k, int Kp, const __nv_bfloat16* t, bool neg) {
     for (int q = 0; q < NS; ++q)
       *reinterpret_cast<__nv_bfloat16*>(Ar[q] + tc::kmaj_off(row, k, Kp)) = neg ? __hneg(t[q]) : t[q];
@@ -216,22 +219,37 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     }
     tc::tmem_wait_st();
   };
-  // B1 = V_real^T (K-major, K index = R) from a V state slot
+  // B1 = V_real^T, MN-major: for K index R (this lane's row of V_real), the
+  // N entries c are contiguous in 16-byte rows of 8, so the lane stores each
+  // 8-column piece of a split term with one 16-byte store.  Core matrices:
+  // 8 K-rows x 16 B; stride 128 B along N, (Np/8) 128 B along K.
+  auto put_B1 = [&](int cc, const float* v) {
+    if (R >= T.K1p) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      __nv_bfloat16 t[8][3];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = cc * 16 + h * 8 + j;
+        split(c < n ? v[h * 8 + j] : 0.f, t[j]);
+      }
+      const int cb = cc * 2 + h;  // 8-column block
+      const int off = (R >> 3) * (Np / 8) * 128 + cb * 128 + (R & 7) * 16;
+      for (int q = 0; q < NS; ++q) {
+        uint4 w;
+        w.x = pack_bf16x2(t[0][q], t[1][q]);
+        w.y = pack_bf16x2(t[2][q], t[3][q]);
+        w.z = pack_bf16x2(t[4][q], t[5][q]);
+        w.w = pack_bf16x2(t[6][q], t[7][q]);
+        *reinterpret_cast<uint4*>(Bs[q] + off) = w;
+      }
+    }
+  };
   auto write_B1 = [&](unsigned col) {
     for (int cc = half; cc < nchunks; cc += 2) {
       float v[16];
       tc::tmem_ld16(lane_addr + col + cc * 16, v);
-      if (R < T.K1p) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = cc * 16 + j;
-          if (c < n) {
-            __nv_bfloat16 t[3];
-            split(v[j], t);
-            put(Bs, c, R, T.K1p, t, false);
-          }
-        }
-      }
+      put_B1(cc, v);
     }
   };
   unsigned phase = 0;
@@ -239,25 +257,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   const int npairs = (NS == 1) ? 1 : (NS == 2 ? 3 : 6);
   const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
   // D = A * B over Kp; mn: A is the MN-major view of the forward operand (H_real^T)
-  auto gemm = [&](unsigned dcol, unsigned char* const* Ar, int Kp, bool mn) -> bool {
+  auto gemm = [&](unsigned dcol, unsigned char* const* Ar, int Kp, bool mn, bool bmn) -> bool {
     // operands written by the threads -> visible to the tensor core
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t idesc = tc::idesc_bf16(128, Np) | (mn ? (1u << 15) : 0u);
+      const uint32_t idesc = tc::idesc_bf16(128, Np) | (mn ? (1u << 15) : 0u) | (bmn ? (1u << 16) : 0u);
       // no swizzle: LBO is the stride between core matrices along K, SBO along M/N,
       // for K-major and MN-major operands alike
-      const unsigned sbo_b = (unsigned)(Kp / 8) * 128u;
+      const unsigned kmaj_sbo = (unsigned)(Kp / 8) * 128u;
       const unsigned lbo_a = mn ? (unsigned)(T.K1p / 8) * 128u : 128u;
-      const unsigned sbo_a = mn ? 128u : sbo_b;
+      const unsigned sbo_a = mn ? 128u : kmaj_sbo;
+      const unsigned lbo_b = bmn ? (unsigned)(Np / 8) * 128u : 128u;
+      const unsigned sbo_b = bmn ? 128u : kmaj_sbo;
       for (int kk = 0; kk < Kp / 16; ++kk) {
         const unsigned aoff = mn ? (unsigned)kk * 2u * lbo_a : (unsigned)kk * 256u;
-        const unsigned boff = (unsigned)kk * 256u;
+        const unsigned boff = bmn ? (unsigned)kk * 2u * lbo_b : (unsigned)kk * 256u;
         for (int q = 0; q < npairs; ++q) {
           tc::mma_bf16(tbase + dcol, tc::smem_desc(tc::su32(Ar[pa[q]]) + aoff, lbo_a, sbo_a),
-                       tc::smem_desc(tc::su32(Bs[pb[q]]) + boff, 128u, sbo_b), idesc, (kk > 0 || q > 0) ? 1u : 0u);
+                       tc::smem_desc(tc::su32(Bs[pb[q]]) + boff, lbo_b, sbo_b), idesc, (kk > 0 || q > 0) ? 1u : 0u);
         }
       }
       tc::commit(&mbar);
@@ -281,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   tc::fence_after_sync();
   if (p.extrapolate && s_ctrl[0] >= 3) {
     write_B1(colV[1]);
-    gemm(colD1[1], A1, T.K1p, false);  // Z(V^{t-2})
+    gemm(colD1[1], A1, T.K1p, false, true);  // Z(V^{t-2})
   }
   write_B1(colV[0]);
 
@@ -290,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     const int t = s_ctrl[0];
     const float omega = (p.extrapolate && t >= 3) ? (float)(t - 2) / (float)(t + 1) : 0.f;
     // ---- S2: Z = H V^{t-1} on the tensor cores
-    if (!gemm(colD1[zc], A1, T.K1p, false)) break;
+    if (!gemm(colD1[zc], A1, T.K1p, false, true)) break;
     // accumulator -> FP32 Z in shared memory (lane R < m: Re row R; m <= R < 2m: Im row R - m)
     for (int cc = half; cc < nchunks; cc += 2) {
       float v[16];
@@ -337,12 +357,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     // ---- S6: B2 = Y_real^T (K-major, K index: Re rows then Im rows)
     gradient_rhs_phase(
         D, Ly, [&](int row, int c) { return Zs[(long long)row * ldz + c]; }, sU, sP, alpha_u,
-        [&](int row, int c, float2 y) {
-          __nv_bfloat16 t[3];
-          split(y.x, t);
-          put(Bs, c, row, T.K2p, t, false);
-          split(y.y, t);
-          put(Bs, c, m + row, T.K2p, t, false);
+        [&](int r, int c, const float2* y) {
+          const int Nr = D.Nr;
+          if (Nr == 4) {
+            // four consecutive K entries (rows r*4..r*4+3, then m + r*4..) share
+            // one 8-byte piece of a core-matrix row: one store per split term
+            __nv_bfloat16 tr[4][3], ti[4][3];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              split(y[a].x, tr[a]);
+              split(y[a].y, ti[a]);
+            }
+            for (int q = 0; q < NS; ++q) {
+              uint2 wr, wi;
+              wr.x = pack_bf16x2(tr[0][q], tr[1][q]);
+              wr.y = pack_bf16x2(tr[2][q], tr[3][q]);
+              wi.x = pack_bf16x2(ti[0][q], ti[1][q]);
+              wi.y = pack_bf16x2(ti[2][q], ti[3][q]);
+              *reinterpret_cast<uint2*>(Bs[q] + tc::kmaj_off(c, r * 4, T.K2p)) = wr;
+              *reinterpret_cast<uint2*>(Bs[q] + tc::kmaj_off(c, m + r * 4, T.K2p)) = wi;
+            }
+          } else {
+            for (int a = 0; a < Nr; ++a) {
+              __nv_bfloat16 t[3];
+              split(y[a].x, t);
+              put(Bs, c, r * Nr + a, T.K2p, t, false);
+              split(y[a].y, t);
+              put(Bs, c, m + r * Nr + a, T.K2p, t, false);
+            }
+          }
         });
     for (int e = tid; e < n * (T.K2p - 2 * m); e += blockDim.x) {  // K padding of B2
       const int c = e / (T.K2p - 2 * m), k = 2 * m + e % (T.K2p - 2 * m);
@@ -390,9 +433,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       if (tid == 0) cellf[0] = gk;
     }
     // ---- S6/S7: G = H^H Y on the tensor cores
-    if (!gemm(colD2, T.mn ? A1 : A2, T.K2p, T.mn)) break;
+    if (!gemm(colD2, T.mn ? A1 : A2, T.K2p, T.mn, false)) break;
     const float gj = cellf[0];
     float nrm = 0.f;
+    // Vtilde = Vhat - gamma G into the V^{t-2} slot and the block's ||Vtilde||^2
     for (int cc = half; cc < nchunks; cc += 2) {
       float g[16], v[16], vp[16];
       tc::tmem_ld16(lane_addr + colD2 + cc * 16, g);
@@ -411,6 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     }
     tc::tmem_wait_st();
     const double s = block_sum((double)nrm, red);
+    // projection (eq. (15)), then B1 = split(V^t) for the next forward GEMM
     const float scale = (s > (double)Pc) ? (float)sqrt((double)Pc / s) : 1.f;
     for (int cc = half; cc < nchunks; cc += 2) {
       float v[16];
@@ -420,11 +465,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
         for (int j = 0; j < 16; ++j) v[j] *= scale;
         tc::tmem_st16(lane_addr + colV[cur ^ 1] + cc * 16, v);
       }
+      put_B1(cc, v);
     }
     tc::tmem_wait_st();
-    cur ^= 1;
-    zc ^= 1;
-    write_B1(colV[cur]);
     if (tid == 0) {
       s_rhoprev = rho;
       s_ctrl[3] = stage;
@@ -433,6 +476,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     }
     tc::fence_before_sync();
     __syncthreads();
+    cur ^= 1;
+    zc ^= 1;
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -338,8 +338,8 @@ static amm::IterParams base_params(amm_ctx* c) {
   p.Lws = c->Lws;
   p.sc = c->sc;
   p.gamma_c = c->gamma_c;
-  p.eps1 = (float)c->opts.eps1;
-  p.eps2 = (float)c->opts.eps2;
+  p.eps1 = c->opts.eps1;
+  p.eps2 = c->opts.eps2;
   p.gamma_user = (float)c->opts.gamma_c;
   p.tc = c->opts.tc;
   p.extrapolate = c->opts.extrapolate;

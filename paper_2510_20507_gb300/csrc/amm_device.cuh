@@ -666,8 +666,8 @@ struct Views {
 // slots (2 Nt).  Contains __syncthreads(); FP32 reductions only.
 template <class HGet>
 __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, const float2* sU, const float2* sP,
-                              const float* alpha_u, float2* QL, float2* y, float2* z, float* ta, float* tb, double* red,
-                              float* bcast) {
+                              const float* alpha_u, float2* QL, float2* y, float2* z, float2* sD, float* ta,
+                              float* tb, double* red, float* bcast) {
   const int Nt = D.Nt, m = Ly.m, Nr = D.Nr, d = D.d;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   float* redf = reinterpret_cast<float*>(red);
@@ -681,6 +681,14 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
   int gN = 1;
   while (gN < 32 && 2 * gN * Nt <= (int)blockDim.x) gN <<= 1;
   float2* slot[2] = {QL, QL + Nt};
+  // D_r = 2 alpha_r P_r U_r^H (Nr x Nr per user), once per call
+  for (int e = tid; e < Ly.CK * Nr * Nr; e += blockDim.x) {
+    const int r = e / (Nr * Nr), ab = e - r * Nr * Nr, a = ab / Nr, b = ab - a * Nr;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < d; ++s) acc = cfma(sP[(r * Nr + a) * d + s], make_float2(sU[(r * Nr + b) * d + s].x,
+                                                                              -sU[(r * Nr + b) * d + s].y), acc);
+    sD[e] = cscale(acc, 2.f * alpha_u[r]);
+  }
   // fixed start vector: unit-modulus entries with golden-ratio phases; q_{-1} = 0
   const float rn = rsqrtf((float)Nt);
   for (int p = tid; p < Nt; p += blockDim.x) {
@@ -708,9 +716,16 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
       const int e = e0 + tid;
       const bool act = e < m * g;
       const int i = act ? e / g : 0, l = e % g;
-      float2 acc = make_float2(0.f, 0.f);
-      if (act)
-        for (int p = l; p < Nt; p += g) acc = cfma(hget(i, p), qj[p], acc);
+      float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+      if (act) {  // two independent chains
+        int p = l;
+        for (; p + g < Nt; p += 2 * g) {
+          acc = cfma(hget(i, p), qj[p], acc);
+          acc1 = cfma(hget(i, p + g), qj[p + g], acc1);
+        }
+        if (p < Nt) acc = cfma(hget(i, p), qj[p], acc);
+        acc = cadd(acc, acc1);
+      }
       for (int o = g >> 1; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, g);
         acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, g);
@@ -722,19 +737,13 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
       settled = true;
       break;
     }
-    // z_r = 2 alpha_r P_r (U_r^H y_r), and a_j = sum_i Re(conj(y_i) z_i)
+    // z_r = D_r y_r, and a_j = sum_i Re(conj(y_i) z_i)
     float apart = 0.f;
     for (int i = tid; i < m; i += blockDim.x) {
       const int r = i / Nr, a = i - r * Nr;
-      const float2* Ur = sU + r * Nr * d;
-      const float2* Pr = sP + r * Nr * d;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int s = 0; s < d; ++s) {
-        float2 ts = make_float2(0.f, 0.f);
-        for (int b = 0; b < Nr; ++b) ts = cjfma(Ur[b * d + s], y[r * Nr + b], ts);
-        acc = cfma(Pr[a * d + s], ts, acc);
-      }
-      const float2 zi = cscale(acc, 2.f * alpha_u[r]);
+      const float2* Dr = sD + (r * Nr + a) * Nr;
+      float2 zi = make_float2(0.f, 0.f);
+      for (int b = 0; b < Nr; ++b) zi = cfma(Dr[b], y[r * Nr + b], zi);
       z[i] = zi;
       const float2 yi = y[i];
       apart = fmaf(yi.x, zi.x, fmaf(yi.y, zi.y, apart));
@@ -751,9 +760,16 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
       const int e = e0 + tid;
       const bool act = e < Nt * gN;
       const int p = act ? e / gN : 0, l = e % gN;
-      float2 acc = make_float2(0.f, 0.f);
-      if (act)
-        for (int i = l; i < m; i += gN) acc = cjfma(hget(i, p), z[i], acc);
+      float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+      if (act) {  // two independent chains
+        int i = l;
+        for (; i + gN < m; i += 2 * gN) {
+          acc = cjfma(hget(i, p), z[i], acc);
+          acc1 = cjfma(hget(i + gN, p), z[i + gN], acc1);
+        }
+        if (i < m) acc = cjfma(hget(i, p), z[i], acc);
+        acc = cadd(acc, acc1);
+      }
       for (int o = gN >> 1; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, gN);
         acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, gN);
@@ -927,17 +943,19 @@ __device__ __forceinline__ bool need_rate(int stage, int mode, int it, int n_ite
   return stage != 2 || mode != kFixed || it + 1 == n_iters;
 }
 
-__device__ __forceinline__ void stage_logic(int* ctrl, double rho, double rho_prev, int mode, float eps1,
-                                            float eps2, int switch_iter, int step_rule, int tc) {
+__device__ __forceinline__ void stage_logic(int* ctrl, double rho, double rho_prev, int mode, double eps1,
+                                            double eps2, int switch_iter, int step_rule, int tc) {
+  // |R^t - R^{t-1}| / R^{t-1} <= eps, tested as |R^t - R^{t-1}| <= eps |R^{t-1}|
+  // (no FP64 division on the single thread that runs this)
   const int t = ctrl[0];
   const bool have_prev = !isnan(rho_prev);
-  const double rel = have_prev ? fabs(rho - rho_prev) / fabs(rho_prev) : INFINITY;
+  const double diff = fabs(rho - rho_prev), ref = fabs(rho_prev);
   int stop = 0;
-  if (mode == kTolerance && ctrl[3] == 2 && rel <= (double)eps2) stop = 1;
+  if (mode == kTolerance && ctrl[3] == 2 && have_prev && ref > 0.0 && diff <= eps2 * ref) stop = 1;
   int stage = ctrl[1], si = ctrl[2];
   if (!stop) {
     if (stage == 1) {
-      const bool go = (switch_iter >= 1) ? (t >= switch_iter) : (rel <= (double)eps1);
+      const bool go = (switch_iter >= 1) ? (t >= switch_iter) : (have_prev && ref > 0.0 && diff <= eps1 * ref);
       if (go) {
         stage = 2;
         si = 0;

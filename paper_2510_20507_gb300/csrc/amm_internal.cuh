@@ -59,7 +59,8 @@ struct IterParams {
   int* iters_out;      // per instance (mode kTolerance), may be null
   int n_iters;
   int mode;
-  float eps1, eps2, gamma_user;
+  double eps1, eps2;
+  float gamma_user;
   int tc, extrapolate, switch_iter, step_rule, lanczos_steps, gemm_tile;
   int smem_budget;
   long long spin_budget;
@@ -93,7 +94,7 @@ __host__ __device__ inline int lanczos_elems(const InstDesc& D) { return 2 * D.N
 struct Layout {
   int m, n, Cn, CK, np, Lm;
   int ldh, ldv, ldz;
-  int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_tri, off_alpha;
+  int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_D, off_tri, off_alpha;
   int off_H, off_V, off_Z, off_L;
   int total;
 };
@@ -118,6 +119,7 @@ __host__ __device__ inline Layout plan_layout(const InstDesc& D, int budget, int
   L.off_rho = off;  off += L.CK * 8;
   L.off_y = off;    off += L.m * 8;
   L.off_z = off;    off += L.m * 8;
+  L.off_D = off;    off += L.CK * D.Nr * D.Nr * 8;
   L.off_tri = off;  off += 2 * (L.Lm + 1) * 4;
   off = align_up(off, 16);
   L.off_alpha = off; off += L.CK * 4;

@@ -182,8 +182,8 @@ extern "C" amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const a
   p.Lws = Lws;
   p.sc = sc;
   p.gamma_c = gamma_c;
-  p.eps1 = (float)o.eps1;
-  p.eps2 = (float)o.eps2;
+  p.eps1 = o.eps1;
+  p.eps2 = o.eps2;
   p.gamma_user = (float)o.gamma_c;
   p.tc = o.tc;
   p.extrapolate = o.extrapolate;

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   double* sRho = reinterpret_cast<double*>(smem + Ly.off_rho);
   float2* ly = reinterpret_cast<float2*>(smem + Ly.off_y);
   float2* lz = reinterpret_cast<float2*>(smem + Ly.off_z);
+  float2* lD = reinterpret_cast<float2*>(smem + Ly.off_D);
   float* ta = reinterpret_cast<float*>(smem + Ly.off_tri);
   float* tb = ta + (Ly.Lm + 1);
 
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
       if (sflag & 1) {
         const float2* Hk = vw.H + (long long)k * m * ldh;
         const float lam = lanczos_norm(
-            D, Ly, [&](int i, int q) { return Hk[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, ta, tb,
+            D, Ly, [&](int i, int q) { return Hk[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, lD, ta, tb,
             red, &s_bcast);
         gk = (lam > 0.f) ? 1.f / lam : 0.f;
         if ((sflag & 2) && tid == 0) gamma_c[k] = gk;

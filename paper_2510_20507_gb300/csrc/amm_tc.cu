@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   double* sRho = reinterpret_cast<double*>(smem + Ly.off_rho);
   float2* ly = reinterpret_cast<float2*>(smem + Ly.off_y);
   float2* lz = reinterpret_cast<float2*>(smem + Ly.off_z);
+  float2* lD = reinterpret_cast<float2*>(smem + Ly.off_D);
   float* ta = reinterpret_cast<float*>(smem + Ly.off_tri);
   float* tb = ta + (Ly.Lm + 1);
   unsigned char* A1[3] = {smem + T.off_A1[0], smem + T.off_A1[1], smem + T.off_A1[2]};
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
           }
           __syncthreads();
           lam = lanczos_norm(
-              D, Ly, [&](int i, int q) { return Zs[(long long)i * ldz + q]; }, sU, sP, alpha_u, QL, ly, lz, ta, tb,
+              D, Ly, [&](int i, int q) { return Zs[(long long)i * ldz + q]; }, sU, sP, alpha_u, QL, ly, lz, lD, ta, tb,
               red, &s_bcast);
         } else {
           lam = lanczos_norm(
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
                 }
                 return make_float2(re, im);
               },
-              sU, sP, alpha_u, QL, ly, lz, ta, tb, red, &s_bcast);
+              sU, sP, alpha_u, QL, ly, lz, lD, ta, tb, red, &s_bcast);
         }
         gk = (lam > 0.f) ? 1.f / lam : 0.f;
         if ((sflag & 2) && tid == 0) gamma_c[0] = gk;

@@ -44,6 +44,29 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
     return 2 * 8 * m * Nt * n * C
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per instance of
+# the iteration kernels, from the ncu captures summarised in profiles/
+# (1216 instances of the timed shape; traffic grows with the instance count,
+# so a full launch is this times its instances).  Valid only for the kernel
+# sources the captures ran: see kernel_digest().
+TRAFFIC = {"digest": "df9594fba90124e5",
+           "tc_iterate_kernel": (120.337408e6 + 31.269632e6) / 1216,
+           "iterate_kernel": (120.554752e6 + 28.694528e6) / 1216}
+
+
+def kernel_digest():
+    """First 16 hex digits of the sha256 over the kernel sources."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2510_20507_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def rank_base_seed(rank):
     """Each rank solves its own disjoint set of instances (weak scaling)."""
     return 2 + 1000 * rank
@@ -400,16 +423,18 @@ def run_gpu(args):
     flops_launch = algorithmic_gemm_flops(C, K, Nt, Nr, d) * ITERS * batch
     avg_iter_ms = statistics.mean(iter_ms)
     achieved = flops_launch / (avg_iter_ms / 1000.0) / 1e12
+    kname = "iterate_kernel" if args.precision == "fp32" else "tc_iterate_kernel"
+    traffic = TRAFFIC[kname] * batch if kernel_digest() == TRAFFIC["digest"] else None
     if args.precision == "fp32":
         peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "iterate_kernel",
+                "traffic": traffic, "kernel": "iterate_kernel",
                 "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                              f"(derived; {src} clocks)"}
     else:
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tc_iterate_kernel", "peak_note": f"bf16 burst, {src}"}
+                "traffic": traffic, "kernel": "tc_iterate_kernel", "peak_note": f"bf16 burst, {src}"}
 
     # ---- the CPU baseline: the oracle on a sample of this batch (every
     #      stride-th instance, all seven P values), timed; its results are
@@ -459,12 +484,64 @@ def run_gpu(args):
     return 0
 
 
+def run_unrolled(args):
+    """The differentiable unrolled workload: 1024 instances of Nt=64, K=16,
+    Nr=2, d=2 at 20 dB, T=20 iterations, checkpoints every 5, forward
+    (WSR) plus the hand-written adjoint (gradients in every gamma_t and in
+    H) per step.  Metric: instance-gradients/s (one JSON line)."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2510_20507_gb300 as pkg
+    from paper_2510_20507_gb300.unrolled import unrolled_wsr
+    T, ck, sw, n = 20, 5, 4, args.instances or 1024
+    insts = wl.unrolled_64(n=n)
+    dev = torch.device("cuda", 0)
+    H = torch.from_numpy(np.stack([i.H[0] for i in insts]).astype(np.complex64)).to(dev).requires_grad_(True)
+    al = torch.from_numpy(np.stack([i.alpha for i in insts]).astype(np.float32)).to(dev)
+    s2 = torch.from_numpy(np.stack([i.sigma2 for i in insts]).astype(np.float32)).to(dev)
+    P = torch.from_numpy(np.array([i.P[0] for i in insts], dtype=np.float32)).to(dev)
+    G0 = np.stack([i.G0[0] for i in insts]).astype(np.complex64)
+    scale = np.sqrt(np.minimum(1.0, P.cpu().numpy() / (np.abs(G0) ** 2).sum(axis=(1, 2))))
+    V0 = torch.from_numpy((G0 * scale[:, None, None]).astype(np.complex64)).to(dev)  # eq. (15) projection
+    gam = torch.full((T,), 0.004, dtype=torch.float32, device=dev, requires_grad=True)
+    solver = pkg.UnrolledSolver(n, (1, 16, 64, 2, 2), T, ckpt_every=ck, switch_iter=sw)
+
+    def step():
+        H.grad = None
+        gam.grad = None
+        unrolled_wsr(solver, H, gam, al, s2, P, V0).sum().backward()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"metric": "instance-gradients/s (unrolled A-MMMSE, forward + adjoint)",
+                      "value": n * args.steps / (ms / 1000.0), "unit": "instance-gradients/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "unrolled: Nt=64, K=16, Nr=2, d=2, P=20 dB, T=20, checkpoints every 5, "
+                                             "stage II from iteration 4", "instances": n}}))
+    solver.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "unrolled"],
+                    help="sweep: the timed P-sweep solve (default); unrolled: the differentiable unrolled workload")
     ap.add_argument("--precision", default="bf16x6", choices=["fp32", "bf16", "bf16x3", "bf16x6"])
     ap.add_argument("--smem-budget", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -483,6 +560,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "unrolled":
+        return run_unrolled(args)
     return run_gpu(args)
 
 

@@ -36,7 +36,7 @@ constexpr int kUThreads = 256;
 // Byte offsets of the shared-memory buffers of one instance.
 struct ULayout {
   int H, Va, Vb, Vh, G, B, A1, A2, A3, Hb, Z, Zh, Y, Yb, Zb, Zhb;
-  int Ti, U, W, P, Ub, Pb, red, ld, total;
+  int Ti, Tc, U, W, P, Ub, Pb, red, ld, total;
 };
 
 __host__ __device__ inline int u_take(int& off, int bytes) {
@@ -66,6 +66,7 @@ __host__ __device__ inline ULayout u_layout(int K, int Nt, int Nr, int d) {
   L.Zb = u_take(off, zb);
   L.Zhb = u_take(off, zb);
   L.Ti = u_take(off, K * Nr * Nr * 8);
+  L.Tc = u_take(off, K * Nr * Nr * 8);
   L.U = u_take(off, K * Nr * d * 8);
   L.W = u_take(off, K * d * d * 8);
   L.P = u_take(off, K * Nr * d * 8);
@@ -107,7 +108,7 @@ __device__ __forceinline__ void u_gemm(int M, int N, int KK, AG a, BG b, EP ep) 
 
 struct UView {
   int K, Nt, Nr, d, m, n;
-  float2 *H, *Z, *Zh, *Y, *G, *Ti, *U, *W, *P;
+  float2 *H, *Z, *Zh, *Y, *G, *Ti, *Tc, *U, *W, *P;
   double* ld;  // per user: log det E_r
   const float* alpha;
 };
@@ -130,19 +131,21 @@ __device__ __forceinline__ Z64 zsub(Z64 a, Z64 b) { return zmk(a.x - b.x, a.y - 
 __device__ __forceinline__ float2 zst(Z64 a) { return make_float2((float)a.x, (float)a.y); }
 
 // Cholesky A = L L^H of an n x n Hermitian matrix (lower triangle of A
-// read); returns false on a non-positive pivot.  logdet += log det A.
-__device__ bool z_chol(const Z64* A, Z64* L, int n, double* logdet) {
+// read); returns false on a non-positive pivot.  iL[j] = 1 / L_jj (one FP64
+// rsqrt per pivot, no division), and the pivots L_jj^2 go to piv[j].
+__device__ bool z_chol(const Z64* A, Z64* L, double* iL, double* piv, int n) {
   for (int j = 0; j < n; ++j) {
     double dj = A[j * n + j].x;
     for (int k = 0; k < j; ++k) dj -= L[j * n + k].x * L[j * n + k].x + L[j * n + k].y * L[j * n + k].y;
     if (!(dj > 0.0)) return false;
-    const double lj = sqrt(dj);
-    *logdet += log(dj);
-    L[j * n + j] = zmk(lj, 0.0);
+    const double rj = rsqrt(dj);
+    iL[j] = rj;
+    piv[j] = dj;
+    L[j * n + j] = zmk(dj * rj, 0.0);
     for (int i = j + 1; i < n; ++i) {
       Z64 s = A[i * n + j];
       for (int k = 0; k < j; ++k) s = zsub(s, zmul(L[i * n + k], zmk(L[j * n + k].x, -L[j * n + k].y)));
-      L[i * n + j] = zmk(s.x / lj, s.y / lj);
+      L[i * n + j] = zmk(s.x * rj, s.y * rj);
     }
     for (int i = 0; i < j; ++i) L[i * n + j] = zmk(0.0, 0.0);
   }
@@ -150,41 +153,36 @@ __device__ bool z_chol(const Z64* A, Z64* L, int n, double* logdet) {
 }
 
 // X = A^{-1} B for A = L L^H (n x n), B n x k, all row-major.
-__device__ void z_chol_solve(const Z64* L, int n, const Z64* B, int k, Z64* X) {
+__device__ void z_chol_solve(const Z64* L, const double* iL, int n, const Z64* B, int k, Z64* X) {
   for (int c = 0; c < k; ++c) {
     for (int i = 0; i < n; ++i) {  // L y = b
       Z64 s = B[i * k + c];
       for (int j = 0; j < i; ++j) s = zsub(s, zmul(L[i * n + j], X[j * k + c]));
-      X[i * k + c] = zmk(s.x / L[i * n + i].x, s.y / L[i * n + i].x);
+      X[i * k + c] = zmk(s.x * iL[i], s.y * iL[i]);
     }
     for (int i = n - 1; i >= 0; --i) {  // L^H x = y
       Z64 s = X[i * k + c];
       for (int j = i + 1; j < n; ++j) s = zsub(s, zcmul(L[j * n + i], X[j * k + c]));
-      X[i * k + c] = zmk(s.x / L[i * n + i].x, s.y / L[i * n + i].x);
+      X[i * k + c] = zmk(s.x * iL[i], s.y * iL[i]);
     }
   }
 }
 
-// Per-user solves of one iteration (thread r < K), from Z = H V^{t-1}:
-// T_r = I + Z_r Z_r^H (all columns), U_r = T_r^{-1} Z_own (eq. (9), sigma^2 = 1),
+// Per-user solves of one iteration (thread r < K), from Z = H V^{t-1} and
+// T_r = I + Z_r Z_r^H (all columns, FP32, in X.Tc): U_r = T_r^{-1} Z_own (eq. (9), sigma^2 = 1),
 // E_r = I - U_r^H Z_own, W_r = E_r^{-1} (eq. (10); I in stage I), P_r = U_r W_r.
 // Stores T_r^{-1}, U, W, P and log det E_r.  Returns false on a failed factorisation.
-__device__ bool u_solve_user(const UView& X, int r, bool stage2) {
+__device__ bool u_solve_user(const UView& X, int r, bool stage2, bool want_ld) {
   const int Nr = X.Nr, d = X.d, n = X.n;
   Z64 A[16], L[16], I4[16], Ti[16], Zo[16], Uu[16], E[16], Le[16], Wm[16];
   for (int a = 0; a < Nr; ++a)
     for (int b = 0; b < Nr; ++b) {
-      Z64 s = zmk(a == b ? 1.0 : 0.0, 0.0);
-      for (int c = 0; c < n; ++c) {
-        const Z64 za = zld(X.Z[(r * Nr + a) * n + c]), zb = zld(X.Z[(r * Nr + b) * n + c]);
-        s = zadd(s, zcmul(zb, za));  // z_a conj(z_b)
-      }
-      A[a * Nr + b] = s;
+      A[a * Nr + b] = zld(X.Tc[(r * Nr + a) * Nr + b]);  // FP32 covariance (u_forward_iter)
       I4[a * Nr + b] = zmk(a == b ? 1.0 : 0.0, 0.0);
     }
-  double ldT = 0.0;
-  if (!z_chol(A, L, Nr, &ldT)) return false;
-  z_chol_solve(L, Nr, I4, Nr, Ti);
+  double iLt[4], pv[4];
+  if (!z_chol(A, L, iLt, pv, Nr)) return false;
+  z_chol_solve(L, iLt, Nr, I4, Nr, Ti);
   for (int a = 0; a < Nr; ++a)
     for (int s = 0; s < d; ++s) Zo[a * d + s] = zld(X.Z[(r * Nr + a) * n + r * d + s]);
   for (int a = 0; a < Nr; ++a)
@@ -205,12 +203,12 @@ __device__ bool u_solve_user(const UView& X, int r, bool stage2) {
       E[s * d + u] = h;
       E[u * d + s] = zmk(h.x, -h.y);
     }
-  double ldE = 0.0;
-  if (!z_chol(E, Le, d, &ldE)) return false;
+  double iLe[4], pe[4];
+  if (!z_chol(E, Le, iLe, pe, d)) return false;
   for (int s = 0; s < d; ++s)
     for (int u = 0; u < d; ++u) I4[s * d + u] = zmk(s == u ? 1.0 : 0.0, 0.0);
   if (stage2) {
-    z_chol_solve(Le, d, I4, d, Wm);
+    z_chol_solve(Le, iLe, d, I4, d, Wm);
   } else {
     for (int q = 0; q < d * d; ++q) Wm[q] = I4[q];
   }
@@ -223,22 +221,34 @@ __device__ bool u_solve_user(const UView& X, int r, bool stage2) {
       for (int u = 0; u < d; ++u) acc = zadd(acc, zmul(Uu[a * d + u], Wm[u * d + s]));
       X.P[(r * Nr + a) * d + s] = zst(acc);
     }
-  X.ld[r] = ldE;
+  if (want_ld) {  // log det E_r from the pivots, only where the WSR is read
+    double prod = 1.0;
+    for (int j = 0; j < d; ++j) prod *= pe[j];
+    X.ld[r] = log(prod);
+  }
   return true;
 }
 
 // Forward part of iteration t shared by both passes: Z = H Va, the per-user
 // solves, Vh = Vhat, Zh = H Vhat, Y (eq. (14) form) and G = H^H Y.
 __device__ void u_forward_iter(const UView& X, bool stage2, float omega, const float2* Va, const float2* Vb,
-                               float2* Vh, int* fail) {
+                               float2* Vh, int* fail, bool want_ld = false) {
   const int m = X.m, n = X.n, Nt = X.Nt, Nr = X.Nr, d = X.d, K = X.K;
   u_gemm(m, n, Nt, [&](int r, int p) { return X.H[r * Nt + p]; }, [&](int p, int c) { return Va[p * n + c]; },
          [&](int r, int c, float2 v) { X.Z[r * n + c] = v; });
   for (int e = threadIdx.x; e < Nt * n; e += blockDim.x)
     Vh[e] = make_float2((1.f + omega) * Va[e].x - omega * Vb[e].x, (1.f + omega) * Va[e].y - omega * Vb[e].y);
   __syncthreads();
+  // T_r = I + sum over all columns of z_a conj(z_b), one thread per entry (FP32)
+  for (int e = threadIdx.x; e < K * Nr * Nr; e += blockDim.x) {
+    const int r = e / (Nr * Nr), ab = e - r * Nr * Nr, a = ab / Nr, b = ab - a * Nr;
+    float2 acc = make_float2(a == b ? 1.f : 0.f, 0.f);
+    for (int c = 0; c < n; ++c) acc = cjfma(X.Z[(r * Nr + b) * n + c], X.Z[(r * Nr + a) * n + c], acc);
+    X.Tc[e] = acc;
+  }
+  __syncthreads();
   for (int r = threadIdx.x; r < K; r += blockDim.x)
-    if (!u_solve_user(X, r, stage2)) atomicExch(fail, kNumeric);
+    if (!u_solve_user(X, r, stage2, want_ld)) atomicExch(fail, kNumeric);
   u_gemm(m, n, Nt, [&](int r, int p) { return X.H[r * Nt + p]; }, [&](int p, int c) { return Vh[p * n + c]; },
          [&](int r, int c, float2 v) { X.Zh[r * n + c] = v; });
   __syncthreads();
@@ -287,6 +297,7 @@ __device__ UView u_view(const UParams& p, unsigned char* smem, const ULayout& L,
   X.Y = reinterpret_cast<float2*>(smem + L.Y);
   X.G = reinterpret_cast<float2*>(smem + L.G);
   X.Ti = reinterpret_cast<float2*>(smem + L.Ti);
+  X.Tc = reinterpret_cast<float2*>(smem + L.Tc);
   X.U = reinterpret_cast<float2*>(smem + L.U);
   X.W = reinterpret_cast<float2*>(smem + L.W);
   X.P = reinterpret_cast<float2*>(smem + L.P);
@@ -360,7 +371,7 @@ __global__ void __launch_bounds__(kUThreads) u_forward_kernel(UParams p) {
   // V^T and WSR(V^T) = sum_r alpha_r log det E_r^{-1} at the MMSE receiver
   float2* cT = u_ckpt(p, b, 2 * p.nseg);
   for (int e = threadIdx.x; e < N; e += blockDim.x) cT[e] = Vbuf[ia][e];
-  u_forward_iter(X, true, 0.f, Vbuf[ia], Vbuf[ia], Vh, &s_fail);
+  u_forward_iter(X, true, 0.f, Vbuf[ia], Vbuf[ia], Vh, &s_fail, true);
   double part = 0.0;
   for (int r = threadIdx.x; r < X.K; r += blockDim.x) part += (double)X.alpha[r] * (-X.ld[r]);
   const double w = block_sum(part, red);
@@ -503,21 +514,24 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
         for (int s2 = 0; s2 < d; ++s2) acc = zsub(acc, zmul(Bm[a * d + s2], zmk(Uu[c2 * d + s2].x, -Uu[c2 * d + s2].y)));
         Tb[a * Nr + c2] = acc;
       }
-    // T = I + Z Z^H: Zbar_r = (Tbar + Tbar^H) Z_r; own columns also get Bm - U Ebar
+    // T = I + Z Z^H: Zbar_r = (Tbar + Tbar^H) Z_r (FP32 over the columns);
+    // own columns also get Bm - U Ebar
+    float2 sym[16], ownb[16];
+    for (int a = 0; a < Nr; ++a)
+      for (int c2 = 0; c2 < Nr; ++c2)
+        sym[a * Nr + c2] = zst(zmk(Tb[a * Nr + c2].x + Tb[c2 * Nr + a].x, Tb[a * Nr + c2].y - Tb[c2 * Nr + a].y));
+    for (int a = 0; a < Nr; ++a)
+      for (int s2 = 0; s2 < d; ++s2) {
+        Z64 acc = Bm[a * d + s2];
+        for (int u = 0; u < d; ++u) acc = zsub(acc, zmul(Uu[a * d + u], Eb[u * d + s2]));
+        ownb[a * d + s2] = zst(acc);
+      }
     for (int c = 0; c < n; ++c) {
       const bool own = c >= r * d && c < r * d + d;
       for (int a = 0; a < Nr; ++a) {
-        Z64 acc = zmk(0.0, 0.0);
-        for (int c2 = 0; c2 < Nr; ++c2) {
-          const Z64 sym = zmk(Tb[a * Nr + c2].x + Tb[c2 * Nr + a].x, Tb[a * Nr + c2].y - Tb[c2 * Nr + a].y);
-          acc = zadd(acc, zmul(sym, zld(X.Z[(r * Nr + c2) * n + c])));
-        }
-        if (own) {
-          const int s2 = c - r * d;
-          acc = zadd(acc, Bm[a * d + s2]);
-          for (int u = 0; u < d; ++u) acc = zsub(acc, zmul(Uu[a * d + u], Eb[u * d + s2]));
-        }
-        Zb[(r * Nr + a) * n + c] = zst(acc);
+        float2 acc = own ? ownb[a * d + (c - r * d)] : make_float2(0.f, 0.f);
+        for (int c2 = 0; c2 < Nr; ++c2) acc = cfma(sym[a * Nr + c2], X.Z[(r * Nr + c2) * n + c], acc);
+        Zb[(r * Nr + a) * n + c] = acc;
       }
     }
     for (int q = 0; q < Nr * d; ++q) {

@@ -534,14 +534,63 @@ def run_unrolled(args):
     return 0
 
 
+def run_other(args):
+    """Solve throughput of the other workloads (one JSON line, FP32-GEMM path
+    unless --precision says otherwise): hex7 = 256 seven-cell instances
+    (Nt=128, K=10, Nr=2, d=2, path loss and shadowing), 50 iterations;
+    uneven = 4096 single-cell instances of mixed sizes in one launch
+    (longest first), 30 iterations."""
+    import torch
+    import workloads as wl
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2510_20507_gb300 as pkg
+    if args.workload == "hex7":
+        insts, iters, desc = wl.hex7(n=256), 50, "seven hexagonal cells, Nt=128, K=10, Nr=2, d=2, 256 instances"
+    else:
+        insts, iters, desc = wl.uneven(n=4096), 30, "uneven single-cell batch: Nt 16..256, K 4..64, Nr 1/2/4, 4096"
+    pk = wl.pack(insts)
+    dims = pk.dims[0] if pk.uniform else pk.dims
+    prec = args.precision if args.precision != "bf16x6" else "fp32"  # tensor-core path: single cell, Nt <= 64 only
+    dev = torch.device("cuda", 0)
+    s = pkg.Solver(len(insts), dims, precision=prec, fp64_solves=0 if args.fp32_solves else 1)
+    H, G0 = torch.from_numpy(pk.H).to(dev), torch.from_numpy(pk.G0).to(dev)
+    al, s2, P = (torch.from_numpy(x).to(dev) for x in (pk.alpha, pk.sigma2, pk.P))
+    wsr = torch.empty(len(insts), dtype=torch.float64, device=dev)
+
+    def step():
+        s.set_problem(H, al, s2, P)
+        s.warmstart(G0)
+        s.step(iters)
+        s.wsr(wsr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"metric": "instance-solves/s", "value": len(insts) * args.steps / (ms / 1000.0),
+                      "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": prec, "data": "synthetic",
+                      "config": {"workload": desc, "iterations": iters}}))
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "unrolled"],
-                    help="sweep: the timed P-sweep solve (default); unrolled: the differentiable unrolled workload")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "unrolled", "hex7", "uneven"],
+                    help="sweep: the timed P-sweep solve (default); unrolled: the differentiable unrolled workload; "
+                         "hex7 / uneven: solve throughput of the seven-cell and mixed-size workloads")
     ap.add_argument("--precision", default="bf16x6", choices=["fp32", "bf16", "bf16x3", "bf16x6"])
     ap.add_argument("--smem-budget", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -562,6 +611,8 @@ def main():
         return run_reference(args)
     if args.workload == "unrolled":
         return run_unrolled(args)
+    if args.workload in ("hex7", "uneven"):
+        return run_other(args)
     return run_gpu(args)
 
 

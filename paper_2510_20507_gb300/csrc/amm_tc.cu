@@ -171,8 +171,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     }
     if (NS > 2) t[2] = __float2bfloat16_rn(r);
   };
-  auto pack_bf16x2 = [](__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+  // split two values at once into NS packed bf16 pairs (word q holds term q
+  // of x0 in its low half and of x1 in its high half); the paired
+  // conversion rounds each half exactly as split() does
+  auto split2 = [&](float x0, float x1, unsigned* w) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    w[0] = reinterpret_cast<const unsigned&>(h);
+    if (NS > 1) {
+      x0 -= __low2float(h);
+      x1 -= __high2float(h);
+      h = __floats2bfloat162_rn(x0, x1);
+      w[1] = reinterpret_cast<const unsigned&>(h);
+    }
+    if (NS > 2) {
+      x0 -= __low2float(h);
+      x1 -= __high2float(h);
+      h = __floats2bfloat162_rn(x0, x1);
+      w[2] = reinterpret_cast<const unsigned&>(h);
+    }
   };
   auto put = [&](unsigned char* const* Ar, int row, int k, int Kp, const __nv_bfloat16* t, bool neg) {
     for (int q = 0; q < NS; ++q)
@@ -228,22 +244,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     if (R >= T.K1p) return;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      __nv_bfloat16 t[8][3];
+      unsigned t[4][3];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int c = cc * 16 + h * 8 + j;
-        split(c < n ? v[h * 8 + j] : 0.f, t[j]);
+      for (int j = 0; j < 4; ++j) {
+        const int c = cc * 16 + h * 8 + 2 * j;
+        split2(c < n ? v[h * 8 + 2 * j] : 0.f, c + 1 < n ? v[h * 8 + 2 * j + 1] : 0.f, t[j]);
       }
       const int cb = cc * 2 + h;  // 8-column block
       const int off = (R >> 3) * (Np / 8) * 128 + cb * 128 + (R & 7) * 16;
-      for (int q = 0; q < NS; ++q) {
-        uint4 w;
-        w.x = pack_bf16x2(t[0][q], t[1][q]);
-        w.y = pack_bf16x2(t[2][q], t[3][q]);
-        w.z = pack_bf16x2(t[4][q], t[5][q]);
-        w.w = pack_bf16x2(t[6][q], t[7][q]);
-        *reinterpret_cast<uint4*>(Bs[q] + off) = w;
-      }
+      for (int q = 0; q < NS; ++q)
+        *reinterpret_cast<uint4*>(Bs[q] + off) = make_uint4(t[0][q], t[1][q], t[2][q], t[3][q]);
     }
   };
   auto write_B1 = [&](unsigned col) {
@@ -363,20 +373,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
           if (Nr == 4) {
             // four consecutive K entries (rows r*4..r*4+3, then m + r*4..) share
             // one 8-byte piece of a core-matrix row: one store per split term
-            __nv_bfloat16 tr[4][3], ti[4][3];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-              split(y[a].x, tr[a]);
-              split(y[a].y, ti[a]);
-            }
+            unsigned r01[3], r23[3], i01[3], i23[3];
+            split2(y[0].x, y[1].x, r01);
+            split2(y[2].x, y[3].x, r23);
+            split2(y[0].y, y[1].y, i01);
+            split2(y[2].y, y[3].y, i23);
             for (int q = 0; q < NS; ++q) {
-              uint2 wr, wi;
-              wr.x = pack_bf16x2(tr[0][q], tr[1][q]);
-              wr.y = pack_bf16x2(tr[2][q], tr[3][q]);
-              wi.x = pack_bf16x2(ti[0][q], ti[1][q]);
-              wi.y = pack_bf16x2(ti[2][q], ti[3][q]);
-              *reinterpret_cast<uint2*>(Bs[q] + tc::kmaj_off(c, r * 4, T.K2p)) = wr;
-              *reinterpret_cast<uint2*>(Bs[q] + tc::kmaj_off(c, m + r * 4, T.K2p)) = wi;
+              *reinterpret_cast<uint2*>(Bs[q] + tc::kmaj_off(c, r * 4, T.K2p)) = make_uint2(r01[q], r23[q]);
+              *reinterpret_cast<uint2*>(Bs[q] + tc::kmaj_off(c, m + r * 4, T.K2p)) = make_uint2(i01[q], i23[q]);
             }
           } else {
             for (int a = 0; a < Nr; ++a) {

@@ -142,7 +142,21 @@ static __device__ __noinline__ void stage_rows(float2* dst, int sld, const float
         : "memory");
     if (done || clock64() - t0 > spin_budget) break;
   }
-  if (!done) atomicExch(fail, kTimeout);
+  if (!done) {
+    // report, then let the copies in flight land before anything else uses
+    // (or releases) this shared memory: a second wait with a fixed budget
+    atomicExch(fail, kTimeout);
+    const long long t1 = clock64();
+    while (!done && clock64() - t1 < kDrainBudget) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(smem_u32(mbar)), "r"(phase)
+          : "memory");
+    }
+  }
   phase ^= 1u;
   __syncthreads();
 }

@@ -13,6 +13,10 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxNr = 4;         // Nr <= 4 (small solves are unrolled for 1..4)
 constexpr int kMaxCells = 16;
 constexpr int kMaxLanczos = 64;
+// After a wait ran past spin_budget, the kernel still waits for its own
+// asynchronous copies / tensor-core operations to land, for at most this
+// many SM clock cycles (about two seconds), before it moves on.
+constexpr long long kDrainBudget = 4000000000ll;
 constexpr int kSmemMax = 232448;  // 227 KB dynamic shared memory per block on sm_103
 
 enum Mode { kFixed = 0, kTolerance = 1, kEvalWsr = 2 };

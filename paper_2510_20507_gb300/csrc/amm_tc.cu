@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     tc::fence_after_sync();
     if (!ok) {
       atomicExch(&s_fail, kTimeout);
-      tc::mbar_wait(&mbar, phase ^ 1u, p.spin_budget);  // let the MMAs drain before the block moves on
+      tc::mbar_wait(&mbar, phase ^ 1u, kDrainBudget);  // let the MMAs drain before the block moves on
     }
     __syncthreads();
     return s_fail == kOk;

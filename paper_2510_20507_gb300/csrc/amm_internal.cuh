@@ -99,7 +99,7 @@ struct Layout {
   int m, n, Cn, CK, np, Lm;
   int ldh, ldv, ldz;
   int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_D, off_tri, off_alpha;
-  int off_H, off_V, off_Z, off_L;
+  int off_H, off_Hs, off_V, off_Z, off_L;
   int total;
 };
 
@@ -132,8 +132,17 @@ __host__ __device__ inline Layout plan_layout(const InstDesc& D, int budget, int
   const int szV = 2 * D.C * D.Nt * L.ldv * 8;
   const int szZ = 2 * L.m * L.ldz * 8;
   const int szL = lanczos_elems(D) * 8;
-  L.off_H = L.off_V = L.off_Z = L.off_L = -1;
-  if (off + szH <= budget) { L.off_H = off; off += szH; }
+  // multi-cell instances whose channel does not fit get a staging buffer for
+  // one cell's block Htilde_j instead (staged per GEMM from global memory)
+  const int szHs = L.m * L.ldh * 8;
+  L.off_H = L.off_Hs = L.off_V = L.off_Z = L.off_L = -1;
+  if (off + szH <= budget) {
+    L.off_H = off;
+    off += szH;
+  } else if (D.C > 1 && off + szHs <= budget) {
+    L.off_Hs = off;
+    off += szHs;
+  }
   if (off + szV <= budget) { L.off_V = off; off += szV; }
   if (off + szZ <= budget) { L.off_Z = off; off += szZ; }
   if (off + szL <= budget) { L.off_L = off; off += szL; }

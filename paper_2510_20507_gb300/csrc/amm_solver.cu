@@ -133,14 +133,24 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   }
   int cur = 0;  // V[cur] = V^{t-1}, V[cur^1] = V^{t-2}; Z[zc] = Z(V^{t-1}), Z[zc^1] = Z(V^{t-2})
   int zc = 0;
-  const int ldh = vw.ldh, ldv = vw.ldv, ldz = vw.ldz;
+  const int ldv = vw.ldv, ldz = vw.ldz;
+  // cell j's block Htilde_j: resident, staged into the one-cell buffer (bulk
+  // copy, bounded wait) before each use, or read from global memory
+  float2* sHs = (Ly.off_Hs >= 0) ? reinterpret_cast<float2*>(smem + Ly.off_Hs) : nullptr;
+  const int ldh = sHs ? Ly.ldh : vw.ldh;
+  auto cell_h = [&](int j) -> const float2* {
+    if (!sHs) return vw.H + (long long)j * m * vw.ldh;
+    __syncthreads();  // the previous user of the buffer is done
+    stage_rows(sHs, Ly.ldh, Hg + (long long)j * m * Nt, Nt, m, Nt, &mbar, phase, p.spin_budget, &s_fail);
+    return sHs;
+  };
   const int tile_z = gemm_tile_for(p.gemm_tile, m, n), tile_g = gemm_tile_for(p.gemm_tile, Nt, n);
 
   // Z(V^{t-2}) is needed from t = 3 on (omega > 0); rebuild it once per launch.
   if (p.mode != kEvalWsr && p.extrapolate && s_ctrl[0] >= 3) {
     for (int j = 0; j < C; ++j) {
       float2* Zo = vw.Z[zc ^ 1] + j * n;
-      block_cgemm_tiled<0>(tile_z, m, n, Nt, vw.H + (long long)j * m * ldh, ldh, vw.V[cur ^ 1] + (long long)j * Nt * ldv,
+      block_cgemm_tiled<0>(tile_z, m, n, Nt, cell_h(j), ldh, vw.V[cur ^ 1] + (long long)j * Nt * ldv,
                            ldv, [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
     }
     __syncthreads();
@@ -156,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     // ---- S2: Z = H V^{t-1}
     for (int j = 0; j < C; ++j) {
       float2* Zo = Zc + j * n;
-      block_cgemm_tiled<0>(tile_z, m, n, Nt, vw.H + (long long)j * m * ldh, ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
+      block_cgemm_tiled<0>(tile_z, m, n, Nt, cell_h(j), ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
                            [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
     }
     __syncthreads();
@@ -197,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     for (int k = 0; k < C; ++k) {
       float gk;
       if (sflag & 1) {
-        const float2* Hk = vw.H + (long long)k * m * ldh;
+        const float2* Hk = cell_h(k);
         const float lam = lanczos_norm(
             D, Ly, [&](int i, int q) { return Hk[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, lD, ta, tb,
             red, &s_bcast);
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
       const float2* Vc = vw.V[cur] + (long long)j * Nt * ldv;
       float2* Vn = vw.V[cur ^ 1] + (long long)j * Nt * ldv;
       float nrm = 0.f;
-      block_cgemm_tiled<1>(tile_g, Nt, n, m, vw.H + (long long)j * m * ldh, ldh, Zp + j * n, ldz,
+      block_cgemm_tiled<1>(tile_g, Nt, n, m, cell_h(j), ldh, Zp + j * n, ldz,
                            [&](int r, int c, float2 g) {
                              const long long idx = (long long)r * ldv + c;
                              float2 vh = Vc[idx];

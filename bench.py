@@ -187,6 +187,11 @@ def _spread_worker(args):
     return fp32_spread(_round32(wl.single_cell_64(N_PER_P, first=b, count=1)[0]), iters, reference=ref)
 
 
+def _oracle_serial(jobs):
+    """Several oracle jobs one after the other in one worker (one core)."""
+    return [x for j in jobs for x in _oracle_worker(j)]
+
+
 def make_pool(cores):
     import multiprocessing as mp
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -455,6 +460,14 @@ def run_gpu(args):
                          f"all seven P values), numpy float64 oracle, {ITERS} iterations each, one process per "
                          f"core, {dt:.1f} s"}
         parity.update(gap_check(pool, {b: got[pos[b]] for b in idx}, res))
+        # the same oracle on one core, on a smaller part of the sample
+        one = idx[::max(1, len(idx) // args.oracle_one_core)][:args.oracle_one_core]
+        if one:
+            t0 = time.perf_counter()
+            n1 = len(pool.apply(_oracle_serial, ([(b, 1, ITERS) for b in one],)))
+            dt1 = time.perf_counter() - t0
+            cpu["one_core"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                               "sample": f"{n1} of those instances in one process, {dt1:.1f} s"}
         pool.close()
 
     line = {
@@ -598,6 +611,8 @@ def main():
                     "the CPU-baseline leg, see --no-cpu-baseline)")
     ap.add_argument("--oracle-sample", type=int, default=1024,
                     help="instances of the batch the CPU-baseline leg solves with the oracle (gap reference)")
+    ap.add_argument("--oracle-one-core", type=int, default=32,
+                    help="instances of that sample solved again in one process (the one-core figure)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 path alongside")
     ap.add_argument("--fp32-solves", action="store_true",

@@ -374,13 +374,19 @@ static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, b
   return false;
 }
 
-// FP64 per-user solve by eight lanes: lane (c, p) of the group owns column c
-// and the real (p = 0) or imaginary (p = 1) part.  Every lane keeps the
-// complex factors whole, but each new complex value is computed one part
-// per lane (two FP64 FMAs per complex multiply-add instead of four) and
-// completed by one exchange with the partner lane (lane ^ 4).  An FP64 warp
-// instruction costs the same for any number of active lanes, so halving the
-// per-lane FP64 work halves the phase.  Same algebra as small_solve_grp.
+// FP64 per-user solve by eight lanes: lane (c, p) of the group works on the
+// real (p = 0) or imaginary (p = 1) part of every complex value it computes,
+// and the partner lane (lane ^ 4) supplies the other part by one exchange.
+// An FP64 warp instruction costs the same for any number of active lanes, so
+// the work per lane is what counts:
+//   * both Cholesky factors are formed row-parallel (lane c computes row c,
+//     the pivot of step j comes from lane j, and each finished column is
+//     broadcast so that every lane ends with the whole factor);
+//   * X = L^{-1} Z_own and UW = L^{-H} X are solved column-parallel (lane c,
+//     column c), and M = X^H X likewise;
+//   * U = UW (I + M)^{-1} is solved row-parallel (lane c, row c of UW, by
+//     v R^H = w then u R = v), so (I + M)^{-1} is never formed.
+// Same algebra as small_solve_grp.
 template <int NR, int DD>
 __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const float2* Zrow0, int ldz, int own0,
                                  float2* U, float2* UW, double* logdet, bool want_u, bool want_ld) {
@@ -390,53 +396,59 @@ __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const
   // s v with s = +1 on the imaginary lane and -1 on the real lane (sign bit flip)
   const unsigned long long smask = p ? 0ull : 0x8000000000000000ull;
   auto sg = [&](double v) { return __longlong_as_double(__double_as_longlong(v) ^ (long long)smask); };
+  // own part of conj(v)
+  auto ownj = [&](C v) { return p ? __longlong_as_double(__double_as_longlong(v.y) ^ (long long)0x8000000000000000ull) : v.x; };
   auto own = [&](C v) { return p ? v.y : v.x; };
   auto oth = [&](C v) { return p ? v.x : v.y; };
   auto join = [&](double o) {
     const double t = __shfl_xor_sync(full, o, 4);
     return p ? mk<double>(t, o) : mk<double>(o, t);
   };
-  // own parts: a*b = a.x own(b) + s a.y oth(b); conj(a) b = a.x own(b) - s a.y oth(b);
-  // a conj(b) = -s a.x own(b) + a.y oth(b)
+  // the whole complex value v of the lanes of column col
+  auto from_col = [&](C v, int col) {
+    const int src = gb + 4 * p + col;
+    return mk<double>(__shfl_sync(full, v.x, src), __shfl_sync(full, v.y, src));
+  };
+  // a positive, finite pivot, tested on its bits (no FP64 compare)
+  auto positive = [](double v) {
+    const long long b = __double_as_longlong(v);
+    return b > 0ll && b < 0x7ff0000000000000ll;
+  };
+  // products by parts (a, b whole): own(a b) = a.x own(b) + s a.y oth(b),
+  // own(conj(a) b) = a.x own(b) - s a.y oth(b), own(a conj(b)) = -s a.x own(b) + a.y oth(b)
   bool ok = act;
+
+  // Q = L L^H, row c of L by lane c; afterwards every lane holds all of L
   C L[NR][NR];
   double inv[NR];
   {
-    C Q[NR][NR];
-    int q = 0;
-#pragma unroll
-    for (int a = 0; a < NR; ++a)
-#pragma unroll
-      for (int b = a; b < NR; ++b) {
-        const float2 v = act ? Qp[q] : make_float2(a == b ? 1.f : 0.f, 0.f);
-        Q[a][b] = join((double)(p ? v.y : v.x));
-        Q[b][a] = cj(Q[a][b]);
-        ++q;
-      }
+    double t0[NR];  // own part of Q[c][j] = conj(Q[j][c]), j <= c
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      double acc = 0.0;
+      float2 v = make_float2(0.f, 0.f);
+      if (j <= c && c < NR) v = act ? Qp[j * NR - (j * (j - 1)) / 2 + (c - j)] : make_float2(j == c ? 1.f : 0.f, 0.f);
+      t0[j] = (double)(p ? -v.y : v.x);
+    }
+    C lrow[NR];
 #pragma unroll
-      for (int k = 0; k < j; ++k) acc = fma(own(L[j][k]), own(L[j][k]), acc);
-      acc += __shfl_xor_sync(full, acc, 4);
-      double dj = Q[j][j].x - acc;
-      if (!(dj > 0.0)) {
+    for (int j = 0; j < NR; ++j) {
+      double t = t0[j];
+#pragma unroll
+      for (int k = 0; k < j; ++k)  // t -= own(L[c][k] conj(L[j][k]))
+        t = fma(-L[j][k].x, own(lrow[k]), fma(sg(L[j][k].y), oth(lrow[k]), t));
+      double dj = __shfl_sync(full, t, gb + j);  // the pivot, from the real lane of row j
+      if (!positive(dj)) {
         ok = false;
         dj = 1.0;
       }
       const double rj = rsqrt(dj);
       inv[j] = rj;
-      L[j][j] = mk<double>(dj * rj, 0.0);
+      lrow[j] = join(t * rj);
 #pragma unroll
-      for (int i = j + 1; i < NR; ++i) {
-        double t = own(Q[i][j]);
-#pragma unroll
-        for (int k = 0; k < j; ++k) t = fma(sg(L[i][k].x), own(L[j][k]), fma(-L[i][k].y, oth(L[j][k]), t));
-        L[i][j] = join(t * rj);
-      }
+      for (int i = j + 1; i < NR; ++i) L[i][j] = from_col(lrow[j], i);
     }
   }
-  // this lane's column of X = L^{-1} Z_own
+  // column c of X = L^{-1} Z_own
   const bool mine = act && c < DD;
   C x[NR];
 #pragma unroll
@@ -447,54 +459,42 @@ __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const
     for (int k = 0; k < i; ++k) t = fma(-L[i][k].x, own(x[k]), fma(-sg(L[i][k].y), oth(x[k]), t));
     x[i] = join(t * inv[i]);
   }
-  // column c of M = X^H X, then every lane gathers M and factors I + M = R R^H
+  // column c of M = X^H X; row c of M is its conjugate (M Hermitian)
   C mcol[DD];
 #pragma unroll
   for (int a = 0; a < DD; ++a) {
     double t = 0.0;
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
-      const int src = gb + 4 * p + a;
-      const C xa = mk<double>(__shfl_sync(full, x[i].x, src), __shfl_sync(full, x[i].y, src));
+      const C xa = from_col(x[i], a);
       t = fma(xa.x, own(x[i]), fma(-sg(xa.y), oth(x[i]), t));
     }
     mcol[a] = join(t);
   }
+  // I + M = R R^H, row c of R by lane c (pivots kept minus one for log1p)
   C R[DD][DD];
   double rinv[DD];
   double mypiv = 0.0;
   {
-    C A[DD][DD];
-#pragma unroll
-    for (int b = 0; b < DD; ++b)
-#pragma unroll
-      for (int a = 0; a < DD; ++a) {
-        const int src = gb + 4 * p + b;
-        A[a][b] = mk<double>(__shfl_sync(full, mcol[a].x, src), __shfl_sync(full, mcol[a].y, src));
-      }
+    C rrow[DD];
 #pragma unroll
     for (int j = 0; j < DD; ++j) {
-      double acc = 0.0;
+      double t = ownj(mcol[j]);
 #pragma unroll
-      for (int k = 0; k < j; ++k) acc = fma(own(R[j][k]), own(R[j][k]), acc);
-      acc += __shfl_xor_sync(full, acc, 4);
-      double dm1 = A[j][j].x - acc;  // pivot - 1
-      if (!(dm1 > -1.0)) {
+      for (int k = 0; k < j; ++k) t = fma(-R[j][k].x, own(rrow[k]), fma(sg(R[j][k].y), oth(rrow[k]), t));
+      double dm1 = __shfl_sync(full, t, gb + j);  // pivot - 1
+      double dj = 1.0 + dm1;
+      if (!positive(dj)) {
         ok = false;
         dm1 = 0.0;
+        dj = 1.0;
       }
       if (j == c) mypiv = dm1;
-      const double dj = 1.0 + dm1;
       const double rj = rsqrt(dj);
       rinv[j] = rj;
-      R[j][j] = mk<double>(dj * rj, 0.0);
+      rrow[j] = join(t * rj);
 #pragma unroll
-      for (int i = j + 1; i < DD; ++i) {
-        double t = own(A[i][j]);
-#pragma unroll
-        for (int k = 0; k < j; ++k) t = fma(sg(R[i][k].x), own(R[j][k]), fma(-R[i][k].y, oth(R[j][k]), t));
-        R[i][j] = join(t * rj);
-      }
+      for (int i = j + 1; i < DD; ++i) R[i][j] = from_col(rrow[j], i);
     }
   }
   // log det(I + M): lane c contributes log1p of pivot c, summed over the columns
@@ -503,7 +503,7 @@ __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const
   ld += __shfl_xor_sync(full, ld, 2);
   if (c == 0 && p == 0) *logdet = ld;
   if (!want_u) return ok;
-  // this lane's column of UW = L^{-H} x
+  // column c of UW = L^{-H} x
   C y[NR];
 #pragma unroll
   for (int i = NR - 1; i >= 0; --i) {
@@ -511,37 +511,37 @@ __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const
 #pragma unroll
     for (int k = i + 1; k < NR; ++k) t = fma(-L[k][i].x, own(y[k]), fma(sg(L[k][i].y), oth(y[k]), t));
     y[i] = join(t * inv[i]);
+    if (mine && ok) reinterpret_cast<float*>(UW + i * DD + c)[p] = (float)own(y[i]);
   }
-  // column c of (I+M)^{-1}: R g = e_c, then R^H m = g
-  C g[DD], mi[DD];
+  // row c of UW (own parts), gathered from the column lanes
+  double w[DD];
 #pragma unroll
-  for (int i = 0; i < DD; ++i) {
-    double t = (p == 0 && i == c) ? 1.0 : 0.0;
+  for (int b = 0; b < DD; ++b) w[b] = 0.0;
 #pragma unroll
-    for (int k = 0; k < i; ++k) t = fma(-R[i][k].x, own(g[k]), fma(-sg(R[i][k].y), oth(g[k]), t));
-    g[i] = join(t * rinv[i]);
-  }
-#pragma unroll
-  for (int i = DD - 1; i >= 0; --i) {
-    double t = own(g[i]);
-#pragma unroll
-    for (int k = i + 1; k < DD; ++k) t = fma(-R[k][i].x, own(mi[k]), fma(sg(R[k][i].y), oth(mi[k]), t));
-    mi[i] = join(t * rinv[i]);
-  }
-  // U[:, c] = sum_b UW[:, b] (I+M)^{-1}[b][c]; each lane stores its part
-#pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    double t = 0.0;
+  for (int i = 0; i < NR; ++i)
 #pragma unroll
     for (int b = 0; b < DD; ++b) {
-      const int src = gb + 4 * p + b;
-      const C uw = mk<double>(__shfl_sync(full, y[i].x, src), __shfl_sync(full, y[i].y, src));
-      t = fma(uw.x, own(mi[b]), fma(sg(uw.y), oth(mi[b]), t));
+      const double v = __shfl_sync(full, own(y[i]), gb + 4 * p + b);
+      if (i == c) w[b] = v;
     }
-    if (mine && ok) {
-      reinterpret_cast<float*>(U + i * DD + c)[p] = (float)t;
-      reinterpret_cast<float*>(UW + i * DD + c)[p] = (float)own(y[i]);
-    }
+  // row c of U = UW (R R^H)^{-1}: v R^H = w, then u R = v
+  C v[DD], u[DD];
+#pragma unroll
+  for (int j = 0; j < DD; ++j) {
+    double t = w[j];
+#pragma unroll
+    for (int k = 0; k < j; ++k)  // t -= own(v_k conj(R[j][k]))
+      t = fma(sg(v[k].x), own(R[j][k]), fma(-v[k].y, oth(R[j][k]), t));
+    v[j] = join(t * rinv[j]);
+  }
+#pragma unroll
+  for (int j = DD - 1; j >= 0; --j) {
+    double t = own(v[j]);
+#pragma unroll
+    for (int k = j + 1; k < DD; ++k)  // t -= own(u_k R[k][j])
+      t = fma(-u[k].x, own(R[k][j]), fma(-sg(u[k].y), oth(R[k][j]), t));
+    u[j] = join(t * rinv[j]);
+    if (act && ok && c < NR) reinterpret_cast<float*>(U + c * DD + j)[p] = (float)own(u[j]);
   }
   return ok;
 }

@@ -49,9 +49,9 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
 # (1216 instances of the timed shape; traffic grows with the instance count,
 # so a full launch is this times its instances).  Valid only for the kernel
 # sources the captures ran: see kernel_digest().
-TRAFFIC = {"digest": "9f84def0157e131b",
-           "tc_iterate_kernel": (120.100352e6 + 31.611648e6) / 1216,
-           "iterate_kernel": (120.448512e6 + 28.646656e6) / 1216}
+TRAFFIC = {"digest": "bf6c190baa0dea6b",
+           "tc_iterate_kernel": (120.443136e6 + 30.831616e6) / 1216,
+           "iterate_kernel": (120.475648e6 + 28.907264e6) / 1216}
 
 
 def kernel_digest():

@@ -52,6 +52,12 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
 TRAFFIC = {"digest": "bf6c190baa0dea6b",
            "tc_iterate_kernel": (120.443136e6 + 30.831616e6) / 1216,
            "iterate_kernel": (120.475648e6 + 28.907264e6) / 1216}
+# pipe utilisation of the same captures (% of peak, ncu --set full), reported
+# beside the roofline while the sources match the digest: which unit is busy
+PIPES = {"tc_iterate_kernel": {"tensor_pct": 4.94, "fp64_pct": 27.0, "fma_pct": 9.5, "dram_pct": 0.15,
+                               "issue_active_pct": 24.2},
+         "iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 16.6, "fma_pct": 28.3, "dram_pct": 0.11,
+                            "issue_active_pct": 40.8}}
 
 
 def kernel_digest():
@@ -429,7 +435,8 @@ def run_gpu(args):
     avg_iter_ms = statistics.mean(iter_ms)
     achieved = flops_launch / (avg_iter_ms / 1000.0) / 1e12
     kname = "iterate_kernel" if args.precision == "fp32" else "tc_iterate_kernel"
-    traffic = TRAFFIC[kname] * batch if kernel_digest() == TRAFFIC["digest"] else None
+    same_sources = kernel_digest() == TRAFFIC["digest"]
+    traffic = TRAFFIC[kname] * batch if same_sources else None
     if args.precision == "fp32":
         peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -440,6 +447,7 @@ def run_gpu(args):
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "tc_iterate_kernel", "peak_note": f"bf16 burst, {src}"}
+    roof["ncu_pipes"] = PIPES[kname] if same_sources else None
 
     # ---- the CPU baseline: the oracle on a sample of this batch (every
     #      stride-th instance, all seven P values), timed; its results are

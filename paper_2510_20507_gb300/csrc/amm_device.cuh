@@ -385,7 +385,8 @@ static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, b
 //   * X = L^{-1} Z_own and UW = L^{-H} X are solved column-parallel (lane c,
 //     column c), and M = X^H X likewise;
 //   * U = UW (I + M)^{-1} is solved row-parallel (lane c, row c of UW, by
-//     v R^H = w then u R = v), so (I + M)^{-1} is never formed.
+//     v R^H = w then u R = v), so (I + M)^{-1} is never formed;
+//   * pivot tests compare bit patterns instead of issuing FP64 compares.
 // Same algebra as small_solve_grp.
 template <int NR, int DD>
 __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const float2* Zrow0, int ldz, int own0,
@@ -567,21 +568,35 @@ static __device__ __noinline__ bool small_solve_pair_dispatch(int Nr, int d, int
 // the pivots matter and the recurrence is backward stable, so the division
 // is the fast approximate one (a few ulp), which shortens the serial chain.
 static __device__ __forceinline__ int sturm_below(const float* a, const float* b, int n, float x, float scale) {
+  const float tiny = 1e-30f * scale;
   int below = 0;
   float q = a[0] - x;
-  if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
+  if (fabsf(q) < tiny) q = -tiny;
   below += q < 0.f;
-  for (int i = 1; i < n; ++i) {
-    q = (a[i] - x) - __fdividef(b[i - 1] * b[i - 1], q);
-    if (fabsf(q) < 1e-30f * scale) q = -1e-30f * scale;
+  auto step = [&](float ai, float bi) {
+    q = (ai - x) - __fdividef(bi * bi, q);
+    if (fabsf(q) < tiny) q = -tiny;
     below += q < 0.f;
+  };
+  // four steps per trip with their entries loaded up front: the loads and
+  // a_i - x, b_i^2 leave the serial chain through q
+  int i = 1;
+  for (; i + 3 < n; i += 4) {
+    const float a1 = a[i], a2 = a[i + 1], a3 = a[i + 2], a4 = a[i + 3];
+    const float b1 = b[i - 1], b2 = b[i], b3 = b[i + 1], b4 = b[i + 2];
+    step(a1, b1);
+    step(a2, b2);
+    step(a3, b3);
+    step(a4, b4);
   }
+  for (; i < n; ++i) step(a[i], b[i - 1]);
   return below;
 }
 
 // Gershgorin upper bound of the spectrum of T.
 static __device__ __forceinline__ float tridiag_gershgorin(const float* a, const float* b, int n) {
   float hi = a[0];
+#pragma unroll 4
   for (int i = 0; i < n; ++i) {
     const float r = (i > 0 ? fabsf(b[i - 1]) : 0.f) + (i + 1 < n ? fabsf(b[i]) : 0.f);
     hi = fmaxf(hi, a[i] + r);
@@ -592,7 +607,7 @@ static __device__ __forceinline__ float tridiag_gershgorin(const float* a, const
 // Multisection on the Sturm count by warp 0, 32 points per round: narrows a
 // bracket [lo, hi] that holds the largest eigenvalue of T (order n) down to
 // FP32 resolution.  Returns the final bracket (x = lower end, y = upper end).
-static __device__ __noinline__ float2 tridiag_top_refine(const float* a, const float* b, int n, float lo, float hi) {
+static __device__ __forceinline__ float2 tridiag_top_refine(const float* a, const float* b, int n, float lo, float hi) {
   const int lane = threadIdx.x & 31;
   if (hi < lo) hi = lo;
   const float scale = fmaxf(fabsf(hi), 1e-30f);
@@ -626,7 +641,7 @@ constexpr float kLanczosBreak = 1e-5f;
 // no eigenvalue reaches x_0 the value moved by less than tol since the last
 // check and the call returns true; otherwise the bracket between the
 // highest x_l reached and the next one is refined and *lb rises to it.
-static __device__ __noinline__ bool tridiag_top_settled(const float* a, const float* b, int n, float* lb) {
+static __device__ __forceinline__ bool tridiag_top_settled(const float* a, const float* b, int n, float* lb) {
   const int lane = threadIdx.x & 31;
   const float base = *lb;
   const float gh = tridiag_gershgorin(a, b, n);
@@ -862,14 +877,22 @@ __device__ __forceinline__ void covariance_phase(const InstDesc& D, const Layout
   }
 }
 
-// S3b/S4: FP64 solves, four lanes per user, then rho = sum alpha_r R_r
-// (block-uniform; 0 when want_ld is false and the rates are skipped).  own-stream block of user r: rows r*Nr.., columns own0..
-// of the Z view (zrow0(r) gives row r*Nr, ldz its row stride).
-template <class T>
+struct NoIdle {
+  __device__ void operator()() const {}
+};
+
+// S3b/S4: the per-user solves (eight lanes per user in FP64, four in FP32),
+// then rho = sum alpha_r R_r (block-uniform; 0 when want_ld is false and the
+// rates are skipped).  The own-stream block of user r is rows r Nr.., columns
+// own0.. of Z (row stride ldz).  Zown: when non-null, the users' own-stream blocks in compact form (user r
+// at Zown + r Nr d, row stride d), read instead of Z.  idle(): run by the
+// warps that hold no user (all of their lanes), before the closing barrier;
+// it must not use block-wide barriers.
+template <class T, class Idle = NoIdle>
 __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& Ly, const float2* Z, int ldz,
                                               const float2* sQ, float2* sU, float2* sUW, double* sRho,
                                               const float* alpha_u, bool want_u, bool want_ld, double* red,
-                                              int* fail) {
+                                              int* fail, const float2* Zown = nullptr, Idle idle = Idle()) {
   const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, np = Ly.np, CK = Ly.CK;
   // An FP64 warp instruction costs the same however few of its lanes are
   // active (on this part about 64 cycles for one warp, and one per 19 cycles
@@ -878,25 +901,30 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
   // FP32 solves four (column).  The trip count is warp-uniform (the solve
   // shuffles).
   constexpr int kLanes = sizeof(T) == 8 ? 8 : 4;
+  bool had_user = false;
   for (int base = 0; base < kLanes * CK; base += blockDim.x) {
     const int e = base + threadIdx.x;
     const bool act = e < kLanes * CK;
     const int r = act ? e / kLanes : 0, c = e & 3, ri = (e / 4) & (kLanes / 4 - 1);
     if (!__any_sync(0xffffffffu, act)) continue;  // warps without a user skip the solve
-    const int own0 = (r / K) * n + (r % K) * d;
+    had_user = true;
+    const int own0 = Zown ? 0 : (r / K) * n + (r % K) * d;
+    const float2* zr = Zown ? Zown + r * Nr * d : Z + (long long)r * Nr * ldz;
+    const int ldr = Zown ? d : ldz;
     double ld = 0.0;
     bool ok;
     if (kLanes == 8)
-      ok = small_solve_pair_dispatch(Nr, d, c, ri, act, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
-                                     sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u, want_ld);
+      ok = small_solve_pair_dispatch(Nr, d, c, ri, act, sQ + r * np, zr, ldr, own0, sU + r * Nr * d,
+                                     sUW + r * Nr * d, &ld, want_u, want_ld);
     else
-      ok = small_solve_dispatch<T>(Nr, d, c, act, sQ + r * np, Z + (long long)r * Nr * ldz, ldz, own0,
-                                   sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u, want_ld);
+      ok = small_solve_dispatch<T>(Nr, d, c, act, sQ + r * np, zr, ldr, own0, sU + r * Nr * d, sUW + r * Nr * d,
+                                   &ld, want_u, want_ld);
     if (act && c == 0 && ri == 0) {
       if (!ok || !isfinite(ld)) atomicExch(fail, kNumeric);
       sRho[r] = ok ? ld : 0.0;
     }
   }
+  if (!had_user) idle();
   __syncthreads();
   double part = 0.0;
   for (int r = threadIdx.x; r < CK; r += blockDim.x) part += (double)alpha_u[r] * sRho[r];
@@ -905,44 +933,59 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
 
 // S6: Y_r = 2 alpha_r P_r (U_r^H zhat_r - S_r) for every user r and stream
 // column c; sink(r, c, y) receives y[a] = Y[r Nr + a][c] for the Nr rows of r.
+// tpu consecutive threads share a user: each keeps U_r and P_r in registers
+// and takes every tpu-th column.
 template <class ZGet, class Sink>
 __device__ __forceinline__ void gradient_rhs_phase(const InstDesc& D, const Layout& Ly, ZGet zhat,
                                                    const float2* sU, const float2* sP, const float* alpha_u,
                                                    Sink sink) {
-  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn;
-  for (int e = threadIdx.x; e < Ly.CK * Cn; e += blockDim.x) {
-    const int r = e / Cn, c = e - r * Cn;
+  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn, CK = Ly.CK;
+  int tpu = (int)blockDim.x / CK;
+  if (tpu < 1) tpu = 1;
+  if (tpu > Cn) tpu = Cn;
+  const int upp = (int)blockDim.x / tpu;  // users per pass
+  const int rr = (int)threadIdx.x / tpu, c0 = (int)threadIdx.x - rr * tpu;
+  for (int r = rr; rr < upp && r < CK; r += upp) {
     const int own0 = (r / K) * n + (r % K) * d;
-    const float2* Ur = sU + r * Nr * d;
-    const float2* Pr = sP + r * Nr * d;
-    float2 zh[kMaxNr];
+    float2 Ur[kMaxNr][kMaxNr], Pr[kMaxNr][kMaxNr];
 #pragma unroll
     for (int a = 0; a < kMaxNr; ++a)
-      if (a < Nr) zh[a] = zhat(r * Nr + a, c);
-    float2 ts[kMaxNr];
 #pragma unroll
-    for (int s = 0; s < kMaxNr; ++s) {
-      if (s < d) {
-        float2 acc = make_float2((c - own0 == s) ? -1.f : 0.f, 0.f);
-#pragma unroll
-        for (int a = 0; a < kMaxNr; ++a)
-          if (a < Nr) acc = cjfma(Ur[a * d + s], zh[a], acc);
-        ts[s] = acc;
-      }
-    }
+      for (int s = 0; s < kMaxNr; ++s)
+        if (a < Nr && s < d) {
+          Ur[a][s] = sU[(r * Nr + a) * d + s];
+          Pr[a][s] = sP[(r * Nr + a) * d + s];
+        }
     const float sc2 = 2.f * alpha_u[r];
-    float2 y[kMaxNr];
+    for (int c = c0; c < Cn; c += tpu) {
+      float2 zh[kMaxNr];
 #pragma unroll
-    for (int a = 0; a < kMaxNr; ++a) {
-      float2 acc = make_float2(0.f, 0.f);
-      if (a < Nr) {
+      for (int a = 0; a < kMaxNr; ++a)
+        if (a < Nr) zh[a] = zhat(r * Nr + a, c);
+      float2 ts[kMaxNr];
 #pragma unroll
-        for (int s = 0; s < kMaxNr; ++s)
-          if (s < d) acc = cfma(Pr[a * d + s], ts[s], acc);
+      for (int s = 0; s < kMaxNr; ++s) {
+        if (s < d) {
+          float2 acc = make_float2((c - own0 == s) ? -1.f : 0.f, 0.f);
+#pragma unroll
+          for (int a = 0; a < kMaxNr; ++a)
+            if (a < Nr) acc = cjfma(Ur[a][s], zh[a], acc);
+          ts[s] = acc;
+        }
       }
-      y[a] = cscale(acc, sc2);
+      float2 y[kMaxNr];
+#pragma unroll
+      for (int a = 0; a < kMaxNr; ++a) {
+        float2 acc = make_float2(0.f, 0.f);
+        if (a < Nr) {
+#pragma unroll
+          for (int s = 0; s < kMaxNr; ++s)
+            if (s < d) acc = cfma(Pr[a][s], ts[s], acc);
+        }
+        y[a] = cscale(acc, sc2);
+      }
+      sink(r, c, y);
     }
-    sink(r, c, y);
   }
 }
 

@@ -35,7 +35,7 @@ struct TcLayout {
   Layout base;  // the small per-user region (offsets from the plain plan)
   int K1p, K2p, Np, Bk, ncols, ns;
   bool mn;
-  int off_A1[3], off_A2[3], off_B[3], off_Zs, off_L, end_ops;
+  int off_A1[3], off_A2[3], off_B[3], off_Zs, off_L, off_Zo, end_ops;
   int total;
   bool ok;
 };
@@ -73,6 +73,11 @@ __host__ __device__ inline TcLayout plan_tc(const InstDesc& D, int budget, int l
   const int szL = lanczos_elems(D) * 8;
   T.off_L = -1;
   if (off + szL <= budget) { T.off_L = off; off += szL; }
+  // the users' own-stream blocks of Z, compact (lets the extrapolation
+  // overwrite the Z staging buffer while the solves run)
+  const int szZo = T.base.CK * D.Nr * D.d * 8;
+  T.off_Zo = -1;
+  if (off + szZo <= budget) { T.off_Zo = off; off += szZo; }
   T.total = off;
   T.ok = D.C == 1 && 2 * m <= 128 && 2 * D.Nt <= 128 && T.ncols <= 512 && off <= budget;
   return T;
@@ -130,6 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   unsigned char* Bs[3] = {smem + T.off_B[0], smem + T.off_B[1], smem + T.off_B[2]};
   float2* Zs = reinterpret_cast<float2*>(smem + T.off_Zs);
   float2* QL = (T.off_L >= 0) ? reinterpret_cast<float2*>(smem + T.off_L) : p.Lws + D.l_off;
+  float2* sZo = (T.off_Zo >= 0) ? reinterpret_cast<float2*>(smem + T.off_Zo) : nullptr;
 
   // per-instance scalars live in shared memory for the whole launch
   float* const s_alpha = reinterpret_cast<float*>(smem + Ly.off_alpha);
@@ -316,6 +322,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   }
   write_B1(colV[0]);
 
+  // the extrapolation can run beside the solves when the users fill warps 0-3
+  // only (eight lanes per user in FP64, four in FP32) and the compact copy fits
+  constexpr int kSolveLanes = sizeof(SolveT) == 8 ? 8 : 4;
+  const bool xo_ok = sZo != nullptr && kSolveLanes * Ly.CK <= 128 && blockDim.x == 256;
   double rho = 0.0;
   for (int it = 0; it < p.n_iters && s_fail == kOk; ++it) {
     const int t = s_ctrl[0];
@@ -335,11 +345,43 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     }
     tc::fence_before_sync();
     __syncthreads();
-    // ---- S3/S4: covariance, FP64 solves, rho = WSR(V^{t-1}), stage test
+    // ---- S3/S4: covariance, FP64 solves, rho = WSR(V^{t-1}), stage test.  When the
+    //      extrapolation overlaps the solves, the users' own-stream blocks are copied
+    //      out of Zs first (one cell: user r owns columns r d ..)
+    const bool overlap = omega != 0.f && xo_ok;
+    if (overlap)
+      for (int e = tid; e < Ly.CK * D.Nr * D.d; e += blockDim.x) {
+        const int row = e / D.d, q = e - row * D.d;
+        sZo[e] = Zs[(long long)row * ldz + (row / D.Nr) * D.d + q];
+      }
     covariance_phase(D, Ly, [&](int row, int c) { return Zs[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
-    rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true,
-                              need_rate(s_ctrl[1], p.mode, it, p.n_iters), red, &s_fail);
+    // ---- S1 overlapped: while warps 0-3 solve, warps 4-7 (no users) form
+    //      Z(Vhat) = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) into Zs, all column chunks
+    //      of their lane quarter; the solves read Z_own from the compact copy
+    auto extrap_idle = [&]() {
+      if (warp < 4) return;
+      tc::fence_after_sync();
+      for (int cc = 0; cc < nchunks; ++cc) {
+        float v[16], vp[16];
+        tc::tmem_ld16(lane_addr + colD1[zc] + cc * 16, v);
+        tc::tmem_ld16(lane_addr + colD1[zc ^ 1] + cc * 16, vp);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = cc * 16 + j;
+          const float zh = (1.f + omega) * v[j] - omega * vp[j];
+          if (c < n && R < m) Zs[(long long)R * ldz + c].x = zh;
+          else if (c < n && R < 2 * m) Zs[(long long)(R - m) * ldz + c].y = zh;
+        }
+      }
+      tc::fence_before_sync();
+    };
+    if (overlap)
+      rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true,
+                                need_rate(s_ctrl[1], p.mode, it, p.n_iters), red, &s_fail, sZo, extrap_idle);
+    else
+      rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true,
+                                need_rate(s_ctrl[1], p.mode, it, p.n_iters), red, &s_fail);
     if (s_fail != kOk) break;
     if (tid == 0)
       stage_logic(s_ctrl, rho, s_rhoprev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
@@ -347,8 +389,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     if (s_ctrl[4]) break;
     const int stage = s_ctrl[1];
     const float2* sP = (stage == 2) ? sUW : sU;
-    // ---- S1: Z(Vhat) = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) into Zs
-    if (omega != 0.f) {
+    // ---- S1: Z(Vhat) = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) into Zs (unless overlapped above)
+    if (omega != 0.f && !overlap) {
       tc::fence_after_sync();
       for (int cc = half; cc < nchunks; cc += 2) {
         float v[16], vp[16];

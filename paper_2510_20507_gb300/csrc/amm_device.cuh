@@ -563,33 +563,50 @@ static __device__ __noinline__ bool small_solve_pair_dispatch(int Nr, int d, int
 
 // ------------------------------------------------------- Lanczos ||F_k||_2
 // Number of eigenvalues of the symmetric tridiagonal T (diagonal a,
-// off-diagonal b, order n) below x: the negative pivots of T - x I (Sturm
-// count, FP32, tiny pivots pushed to the negative side).  Only the signs of
-// the pivots matter and the recurrence is backward stable, so the division
-// is the fast approximate one (a few ulp), which shortens the serial chain.
+// off-diagonal b, order n) below x, by Sylvester's law of inertia: the
+// number of negative pivots of T - x I, i.e. of sign changes in the
+// sequence of leading principal minors p_i = det(T_{0..i} - x I), which obey
+// the three-term recurrence p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}.
+// With T scaled by 1/scale (scale at least about the spectral radius) the
+// entries are O(1), and every second step (p_i, p_{i-1}) is rescaled by an
+// exact power of two, so the values stay in the FP32 range.  The serial
+// chain is one FMA per step (no division); a zero minor counts as positive,
+// which gives the same total as pushing a zero pivot to the negative side.
 static __device__ __forceinline__ int sturm_below(const float* a, const float* b, int n, float x, float scale) {
-  const float tiny = 1e-30f * scale;
-  int below = 0;
-  float q = a[0] - x;
-  if (fabsf(q) < tiny) q = -tiny;
-  below += q < 0.f;
+  const float inv = 1.f / scale;
+  float pm = 1.f, p = (a[0] - x) * inv;
+  int below = (int)(__float_as_uint(p) >> 31);
   auto step = [&](float ai, float bi) {
-    q = (ai - x) - __fdividef(bi * bi, q);
-    if (fabsf(q) < tiny) q = -tiny;
-    below += q < 0.f;
+    const float bs = bi * inv;
+    const float pn = fmaf((ai - x) * inv, p, -(bs * bs) * pm);
+    below += (int)((__float_as_uint(pn) ^ __float_as_uint(p)) >> 31);
+    pm = p;
+    p = pn;
   };
-  // four steps per trip with their entries loaded up front: the loads and
-  // a_i - x, b_i^2 leave the serial chain through q
+  auto renorm = [&]() {
+    const unsigned e = (__float_as_uint(fmaxf(fabsf(p), fabsf(pm))) >> 23) & 0xffu;
+    if (e >= 1u && e <= 253u) {
+      const float f = __uint_as_float((254u - e) << 23);  // 2^(127 - e): exact
+      p *= f;
+      pm *= f;
+    }
+  };
+  // four steps per trip with their entries loaded up front
   int i = 1;
   for (; i + 3 < n; i += 4) {
     const float a1 = a[i], a2 = a[i + 1], a3 = a[i + 2], a4 = a[i + 3];
     const float b1 = b[i - 1], b2 = b[i], b3 = b[i + 1], b4 = b[i + 2];
     step(a1, b1);
     step(a2, b2);
+    renorm();
     step(a3, b3);
     step(a4, b4);
+    renorm();
   }
-  for (; i < n; ++i) step(a[i], b[i - 1]);
+  for (; i < n; ++i) {
+    step(a[i], b[i - 1]);
+    if ((i & 1) == 0) renorm();
+  }
   return below;
 }
 

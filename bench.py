@@ -33,6 +33,8 @@ METRIC = "instance-solves/s at <=1e-3 WSR gap to FP64 oracle vs plain path; % ro
 UNIT = "instance-solves/s"
 ITERS = 50
 N_PER_P = 1024
+HEX7_N, HEX7_ITERS = 256, 50
+UNEVEN_N, UNEVEN_ITERS = 4096, 30
 WORKLOAD = "single-cell P sweep: Nt=64, K=16, Nr=4, d=4, iid CN(0,1), P=0..30 dB (7x1024 instances), 50 iterations"
 
 
@@ -49,27 +51,30 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
 # (1216 instances of the timed shape; traffic grows with the instance count,
 # so a full launch is this times its instances).  Valid only for the kernel
 # sources the captures ran: see kernel_digest().
-TRAFFIC = {"digest": "bf6c190baa0dea6b",
-           "tc_iterate_kernel": (120.443136e6 + 30.831616e6) / 1216,
-           "iterate_kernel": (120.475648e6 + 28.907264e6) / 1216}
+TRAFFIC = {"digest": "11deafb6353144a2",
+           "tc_iterate_kernel": (120.496896e6 + 30.359296e6) / 1216,
+           "iterate_kernel": (120.253184e6 + 28.617984e6) / 1216}
 # pipe utilisation of the same captures (% of peak, ncu --set full), reported
 # beside the roofline while the sources match the digest: which unit is busy
-PIPES = {"tc_iterate_kernel": {"tensor_pct": 4.94, "fp64_pct": 27.0, "fma_pct": 9.5, "dram_pct": 0.15,
-                               "issue_active_pct": 24.2},
-         "iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 16.6, "fma_pct": 28.3, "dram_pct": 0.11,
-                            "issue_active_pct": 40.8}}
+PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.07, "fp64_pct": 28.2, "fma_pct": 8.5, "dram_pct": 0.15,
+                               "issue_active_pct": 25.3},
+         "iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 16.0, "fma_pct": 27.0, "dram_pct": 0.10,
+                            "issue_active_pct": 39.1}}
+
+
+# the sources the iteration kernels and their launches are built from
+DIGEST_SOURCES = ("amm_capi.cu", "amm_device.cuh", "amm_internal.cuh", "amm_solver.cu", "amm_tc.cu", "amm_tc.cuh")
 
 
 def kernel_digest():
-    """First 16 hex digits of the sha256 over the kernel sources."""
+    """First 16 hex digits of the sha256 over the iteration kernels' sources."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2510_20507_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(f.encode())
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in DIGEST_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -166,15 +171,26 @@ def _round32(inst):
     return inst
 
 
-def _oracle_worker(args):
-    """Oracle solves of instances [first, first+count) of the workload:
-    (index, WSR in bits, margin of the stage-I decisions to eps1)."""
-    first, count, iters = args
+def _instances(name, first, count):
+    """Instances [first, first+count) of a named workload."""
     import workloads as wl
+    if name == "hex7":
+        return wl.hex7(n=HEX7_N, first=first, count=count)
+    if name == "uneven":
+        return wl.uneven(n=UNEVEN_N, first=first, count=count)
+    return wl.single_cell_64(N_PER_P, first=first, count=count)
+
+
+def _oracle_worker(args):
+    """Oracle solves of instances [first, first+count) of a workload (the
+    timed sweep unless a name is given): (index, WSR in bits, margin of the
+    stage-I decisions to eps1)."""
+    first, count, iters = args[:3]
+    name = args[3] if len(args) > 3 else "sweep"
     from oracle import solvers as osv
     from oracle import model as om
     out = []
-    for k, inst in enumerate(wl.single_cell_64(N_PER_P, first=first, count=count)):
+    for k, inst in enumerate(_instances(name, first, count)):
         _round32(inst)
         V0 = osv.initial_precoder(inst.G0, inst.P)
         r = osv.ammmse(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0, iters)
@@ -187,10 +203,10 @@ def _oracle_worker(args):
 
 
 def _spread_worker(args):
-    b, iters, ref = args
-    import workloads as wl
+    b, iters, ref = args[:3]
+    name = args[3] if len(args) > 3 else "sweep"
     from oracle.sensitivity import fp32_spread
-    return fp32_spread(_round32(wl.single_cell_64(N_PER_P, first=b, count=1)[0]), iters, reference=ref)
+    return fp32_spread(_round32(_instances(name, b, 1)[0]), iters, reference=ref)
 
 
 def _oracle_serial(jobs):
@@ -222,7 +238,7 @@ def oracle_throughput(pool, cores, n_instances, offset=0):
     return len(res) / dt, dt, len(res)
 
 
-def gap_check(pool, got, oracle_res):
+def gap_check(pool, got, oracle_res, name="sweep", iters=None):
     """The WSR gap of the GPU's solves to the oracle's on the oracle's
     sample.  An instance beyond 1e-3 counts as explained when FP32-sized
     perturbations of the oracle's own arithmetic move its result by more
@@ -231,7 +247,7 @@ def gap_check(pool, got, oracle_res):
     decided = [(b, w) for b, w, mg in oracle_res if mg >= 1e-4]
     gaps = np.array([abs(got[b] - w) / w for b, w in decided])
     over = [(b, w, g) for (b, w), g in zip(decided, gaps) if g > 1e-3]
-    spreads = pool.map(_spread_worker, [(b, ITERS, w) for b, w, _ in over]) if over else []
+    spreads = pool.map(_spread_worker, [(b, iters or ITERS, w, name) for b, w, _ in over]) if over else []
     return {"checked": len(decided), "near_threshold_skipped": len(oracle_res) - len(decided),
             "max_wsr_gap": float(gaps.max()) if len(gaps) else None,
             "p99_wsr_gap": float(np.percentile(gaps, 99)) if len(gaps) else None,
@@ -545,12 +561,25 @@ def run_unrolled(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # roofline: algorithmic flops of a forward + adjoint step = per iteration
+    # the two forward GEMMs (Z = H V, G = H^H Y) and the two adjoint products
+    # of each (C = A B: Abar = Cbar B^H, Bbar = A^H Cbar), six GEMMs of
+    # (K Nr) x Nt x (K d) complex multiply-adds, against the FP32 FFMA peak
+    peaks, src = measured_peaks()
+    flops = 3 * algorithmic_gemm_flops(1, 16, 64, 2, 2) * T * n
+    achieved = flops / (ms / args.steps / 1000.0) / 1e12
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "u_forward_kernel + u_backward_kernel",
+            "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                         f"(derived; {src} clocks)"}
     print(json.dumps({"metric": "instance-gradients/s (unrolled A-MMMSE, forward + adjoint)",
                       "value": n * args.steps / (ms / 1000.0), "unit": "instance-gradients/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "unrolled: Nt=64, K=16, Nr=2, d=2, P=20 dB, T=20, checkpoints every 5, "
-                                             "stage II from iteration 4", "instances": n}}))
+                                             "stage II from iteration 4", "instances": n},
+                      "roofline": roof}))
     solver.close()
     return 0
 
@@ -560,16 +589,25 @@ def run_other(args):
     unless --precision says otherwise): hex7 = 256 seven-cell instances
     (Nt=128, K=10, Nr=2, d=2, path loss and shadowing), 50 iterations;
     uneven = 4096 single-cell instances of mixed sizes in one launch
-    (longest first), 30 iterations."""
+    (longest first), 30 iterations.  With the CPU-baseline leg the oracle
+    solves an evenly spread sample of the batch on the host cores, timed,
+    and its WSR is the reference for the gap of the GPU's solves."""
+    pool, cores = None, os.cpu_count() or 1
+    if not args.no_cpu_baseline:
+        pool = make_pool(cores)  # spawned before the first CUDA call
     import torch
     import workloads as wl
     import __graft_entry__ as ge
     ge.build()
     import paper_2510_20507_gb300 as pkg
-    if args.workload == "hex7":
-        insts, iters, desc = wl.hex7(n=256), 50, "seven hexagonal cells, Nt=128, K=10, Nr=2, d=2, 256 instances"
+    name = args.workload
+    if name == "hex7":
+        insts, iters, desc = wl.hex7(n=HEX7_N), HEX7_ITERS, "seven hexagonal cells, Nt=128, K=10, Nr=2, d=2, 256 instances"
+        sample_n = 32
     else:
-        insts, iters, desc = wl.uneven(n=4096), 30, "uneven single-cell batch: Nt 16..256, K 4..64, Nr 1/2/4, 4096"
+        insts, iters, desc = wl.uneven(n=UNEVEN_N), UNEVEN_ITERS, ("uneven single-cell batch: Nt 16..256, K 4..64, "
+                                                                "Nr 1/2/4, 4096")
+        sample_n = 128
     pk = wl.pack(insts)
     dims = pk.dims[0] if pk.uniform else pk.dims
     prec = args.precision if args.precision != "bf16x6" else "fp32"  # tensor-core path: single cell, Nt <= 64 only
@@ -595,11 +633,40 @@ def run_other(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    got = wsr.cpu().numpy()
+    st = torch.empty(len(insts), dtype=torch.int32, device=dev)
+    s.status(st)
+    n_bad = int((st != 0).sum().item())
+    s.close()
+
+    # roofline: the algorithmic GEMM flops of a whole step (set-up, solve and
+    # WSR evaluation all inside it) against the FP32 FFMA peak
+    peaks, src = measured_peaks()
+    flops = sum(algorithmic_gemm_flops(x.C, x.K, x.Nt, x.Nr, x.d) for x in insts) * iters
+    achieved = flops / (ms / args.steps / 1000.0) / 1e12
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "iterate_kernel",
+            "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                         f"(derived; {src} clocks); achieved over the whole step"}
+
+    cpu, parity = None, {"bad_status": n_bad}
+    if pool is not None:
+        stride = max(1, len(insts) // sample_n)
+        idx = list(range(0, len(insts), stride))[:sample_n]
+        t0 = time.perf_counter()
+        res = [x for r in pool.map(_oracle_worker, [(b, 1, iters, name) for b in idx], chunksize=1) for x in r]
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(res) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(res)} instances of the batch (every {stride}-th), numpy float64 oracle, {iters} "
+                         f"iterations each, one process per core, {dt:.1f} s"}
+        parity.update(gap_check(pool, {b: got[b] for b in idx}, res, name=name, iters=iters))
+        pool.close()
     print(json.dumps({"metric": "instance-solves/s", "value": len(insts) * args.steps / (ms / 1000.0),
                       "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": prec, "data": "synthetic",
-                      "config": {"workload": desc, "iterations": iters}}))
-    s.close()
+                      "config": {"workload": desc, "iterations": iters}, "roofline": roof, "cpu_baseline": cpu,
+                      "parity": parity}))
     return 0
 
 

@@ -253,7 +253,10 @@ def gap_check(pool, got, oracle_res, name="sweep", iters=None):
             "p99_wsr_gap": float(np.percentile(gaps, 99)) if len(gaps) else None,
             "median_wsr_gap": float(np.median(gaps)) if len(gaps) else None,
             "over_1e-3": len(over), "over_1e-3_fp32_sensitive": int(sum(sp > 1e-5 for sp in spreads)),
-            "over_1e-3_unexplained": int(sum(sp <= 1e-5 for sp in spreads))}
+            "over_1e-3_unexplained": int(sum(sp <= 1e-5 for sp in spreads)),
+            # how far beyond the oracle's own spread the GPU lands on those
+            "over_1e-3_max_gap_over_spread": (float(max(g / max(sp, 1e-300) for (_, _, g), sp in zip(over, spreads)))
+                                              if over else None)}
 
 
 def run_reference(args):

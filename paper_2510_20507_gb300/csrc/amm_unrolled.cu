@@ -26,7 +26,7 @@
 #include <string>
 
 #include "../../include/amm.h"
-#include "amm_internal.cuh"
+#include "amm_device.cuh"
 
 namespace amm {
 namespace {
@@ -95,16 +95,12 @@ struct UParams {
   int* status;            // batch
 };
 
-// C(r, c) = sum_p a(r, p) b(p, c), one thread per output element.
-template <class AG, class BG, class EP>
-__device__ __forceinline__ void u_gemm(int M, int N, int KK, AG a, BG b, EP ep) {
-  for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
-    const int r = e / N, c = e - r * N;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int p = 0; p < KK; ++p) acc = cfma(a(r, p), b(p, c), acc);
-    ep(r, c, acc);
-  }
-}
+// Start offset of a lane's sweep over the n columns of rows read with
+// stride n by consecutive lanes.  Without it the 8-byte words of a
+// half-warp share banks whenever n is even (all of them when n is a
+// multiple of 16); with it they fall in distinct banks for n a multiple of
+// 16 and spread out otherwise.  Odd n needs no offset.
+__device__ __forceinline__ int bank_rot(int n) { return (n & 1) ? 0 : (int)(threadIdx.x & 31) % n; }
 
 struct UView {
   int K, Nt, Nr, d, m, n;
@@ -234,8 +230,8 @@ __device__ bool u_solve_user(const UView& X, int r, bool stage2, bool want_ld) {
 __device__ void u_forward_iter(const UView& X, bool stage2, float omega, const float2* Va, const float2* Vb,
                                float2* Vh, int* fail, bool want_ld = false) {
   const int m = X.m, n = X.n, Nt = X.Nt, Nr = X.Nr, d = X.d, K = X.K;
-  u_gemm(m, n, Nt, [&](int r, int p) { return X.H[r * Nt + p]; }, [&](int p, int c) { return Va[p * n + c]; },
-         [&](int r, int c, float2 v) { X.Z[r * n + c] = v; });
+  block_cgemm_tiled<0>(gemm_tile_for(0, m, n), m, n, Nt, X.H, Nt, Va, n,
+                       [&](int r, int c, float2 v) { X.Z[r * n + c] = v; });
   for (int e = threadIdx.x; e < Nt * n; e += blockDim.x)
     Vh[e] = make_float2((1.f + omega) * Va[e].x - omega * Vb[e].x, (1.f + omega) * Va[e].y - omega * Vb[e].y);
   __syncthreads();
@@ -249,8 +245,8 @@ __device__ void u_forward_iter(const UView& X, bool stage2, float omega, const f
   __syncthreads();
   for (int r = threadIdx.x; r < K; r += blockDim.x)
     if (!u_solve_user(X, r, stage2, want_ld)) atomicExch(fail, kNumeric);
-  u_gemm(m, n, Nt, [&](int r, int p) { return X.H[r * Nt + p]; }, [&](int p, int c) { return Vh[p * n + c]; },
-         [&](int r, int c, float2 v) { X.Zh[r * n + c] = v; });
+  block_cgemm_tiled<0>(gemm_tile_for(0, m, n), m, n, Nt, X.H, Nt, Vh, n,
+                       [&](int r, int c, float2 v) { X.Zh[r * n + c] = v; });
   __syncthreads();
   // Y_r = 2 alpha_r P_r (U_r^H Zh_r - S_r), one thread per (user, column)
   for (int e = threadIdx.x; e < K * n; e += blockDim.x) {
@@ -269,8 +265,8 @@ __device__ void u_forward_iter(const UView& X, bool stage2, float omega, const f
     }
   }
   __syncthreads();
-  u_gemm(Nt, n, m, [&](int q, int i) { return make_float2(X.H[i * Nt + q].x, -X.H[i * Nt + q].y); },
-         [&](int i, int c) { return X.Y[i * n + c]; }, [&](int q, int c, float2 v) { X.G[q * n + c] = v; });
+  block_cgemm_tiled<1>(gemm_tile_for(0, Nt, n), Nt, n, m, X.H, Nt, X.Y, n,
+                       [&](int q, int c, float2 v) { X.G[q * n + c] = v; });
   __syncthreads();
 }
 
@@ -425,15 +421,17 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
   gb = block_sum(gb, red);  // also orders the writes of B before the reads below
   if (threadIdx.x == 0) p.gamma_bar[(long long)b * p.T + (t - 1)] = (float)(-gb);
   // Gbar = -gam B;  Ybar = H Gbar
-  u_gemm(m, n, Nt, [&](int r, int q) { return X.H[r * Nt + q]; }, [&](int q, int c) { return B[q * n + c]; },
-         [&](int r, int c, float2 v) { Yb[r * n + c] = cscale(v, -gam); });
+  block_cgemm_tiled<0>(gemm_tile_for(0, m, n), m, n, Nt, X.H, Nt, B, n,
+                       [&](int r, int c, float2 v) { Yb[r * n + c] = cscale(v, -gam); });
   __syncthreads();
   // per user: Abar = 2 alpha P^H Ybar, Ubar, Pbar, Zhbar = U Abar; then W, E and T
   for (int r = threadIdx.x; r < K; r += blockDim.x) {
     const float a2 = 2.f * X.alpha[r];
     float2 ub[16], pb[16];
     for (int q = 0; q < Nr * d; ++q) ub[q] = pb[q] = make_float2(0.f, 0.f);
-    for (int c = 0; c < n; ++c) {
+    const int rot = bank_rot(n);  // lanes hold users: rows r Nr n .. are read with stride Nr n
+    for (int k = 0; k < n; ++k) {
+      const int c = (k + rot < n) ? k + rot : k + rot - n;
       float2 As[kMaxNr], Ab[kMaxNr];
       for (int s2 = 0; s2 < d; ++s2) {
         float2 acc = make_float2(c == r * d + s2 ? -1.f : 0.f, 0.f);
@@ -526,7 +524,8 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
         for (int u = 0; u < d; ++u) acc = zsub(acc, zmul(Uu[a * d + u], Eb[u * d + s2]));
         ownb[a * d + s2] = zst(acc);
       }
-    for (int c = 0; c < n; ++c) {
+    for (int k = 0; k < n; ++k) {
+      const int c = (k + rot < n) ? k + rot : k + rot - n;
       const bool own = c >= r * d && c < r * d + d;
       for (int a = 0; a < Nr; ++a) {
         float2 acc = own ? ownb[a * d + (c - r * d)] : make_float2(0.f, 0.f);
@@ -540,11 +539,15 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
     }
   }
   __syncthreads();
-  // Hbar += Y Gbar^H + Zhbar Vhat^H + Zbar Va^H  (Gbar = -gam B)
+  // Hbar += Y Gbar^H + Zhbar Vhat^H + Zbar Va^H  (Gbar = -gam B).  Lanes hold
+  // consecutive q, so rows q n of B, Vhat, Va are read with stride n; each
+  // lane starts its column sweep at its own offset (bank_rot).
+  const int rot = bank_rot(n);
   for (int e = threadIdx.x; e < m * Nt; e += blockDim.x) {
     const int i = e / Nt, q = e - i * Nt;
     float2 acc = Hb[e];
-    for (int c = 0; c < n; ++c) {
+    for (int k = 0; k < n; ++k) {
+      const int c = (k + rot < n) ? k + rot : k + rot - n;
       const float2 gbar = cscale(B[q * n + c], -gam);
       acc = cfma(X.Y[i * n + c], make_float2(gbar.x, -gbar.y), acc);
       acc = cfma(Zhb[i * n + c], make_float2(Vh[q * n + c].x, -Vh[q * n + c].y), acc);
@@ -595,10 +598,14 @@ __global__ void __launch_bounds__(kUThreads) u_backward_kernel(UParams p) {
     Acc[0][e] = cscale(X.G[e], -wf);
     Acc[1][e] = make_float2(0.f, 0.f);
   }
+  const int rot = bank_rot(X.n);
   for (int e = threadIdx.x; e < X.m * X.Nt; e += blockDim.x) {
     const int i = e / X.Nt, q = e - i * X.Nt;
     float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < X.n; ++c) acc = cfma(X.Y[i * X.n + c], make_float2(Va[q * X.n + c].x, -Va[q * X.n + c].y), acc);
+    for (int k = 0; k < X.n; ++k) {
+      const int c = (k + rot < X.n) ? k + rot : k + rot - X.n;
+      acc = cfma(X.Y[i * X.n + c], make_float2(Va[q * X.n + c].x, -Va[q * X.n + c].y), acc);
+    }
     Hb[e] = cscale(acc, -wf);
   }
   __syncthreads();

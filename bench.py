@@ -51,15 +51,15 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
 # (1216 instances of the timed shape; traffic grows with the instance count,
 # so a full launch is this times its instances).  Valid only for the kernel
 # sources the captures ran: see kernel_digest().
-TRAFFIC = {"digest": "11deafb6353144a2",
-           "tc_iterate_kernel": (120.496896e6 + 30.359296e6) / 1216,
-           "iterate_kernel": (120.253184e6 + 28.617984e6) / 1216}
+TRAFFIC = {"digest": "77cc35857a210341",
+           "tc_iterate_kernel": (120.035072e6 + 30.182656e6) / 1216,
+           "iterate_kernel": (120.429568e6 + 28.571136e6) / 1216}
 # pipe utilisation of the same captures (% of peak, ncu --set full), reported
 # beside the roofline while the sources match the digest: which unit is busy
 PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.07, "fp64_pct": 28.2, "fma_pct": 8.5, "dram_pct": 0.15,
                                "issue_active_pct": 25.3},
-         "iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 16.0, "fma_pct": 27.0, "dram_pct": 0.10,
-                            "issue_active_pct": 39.1}}
+         "iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 18.8, "fma_pct": 27.1, "dram_pct": 0.11,
+                            "issue_active_pct": 40.6}}
 
 
 # the sources the iteration kernels and their launches are built from

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   if (s_fail != kOk) return;
 
   double* red = reinterpret_cast<double*>(smem + Ly.off_red);
-  float* cellf = reinterpret_cast<float*>(smem + Ly.off_cell);  // [0,16): gamma, [16,32): scale
+  float* cellf = reinterpret_cast<float*>(smem + Ly.off_cell);
   float2* sU = reinterpret_cast<float2*>(smem + Ly.off_U);
   float2* sUW = reinterpret_cast<float2*>(smem + Ly.off_UW);
   float2* sQ = reinterpret_cast<float2*>(smem + Ly.off_Q);
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   float* tb = ta + (Ly.Lm + 1);
 
   // per-instance scalars live in shared memory for the whole launch:
-  // cellf[0,16) gamma, [16,32) projection scale, [32,48) P_k, [48,64) gamma_c
+  // cellf[32,48) P_k, [48,64) gamma_c
   float* const s_alpha = reinterpret_cast<float*>(smem + Ly.off_alpha);
   const float* alpha_u = s_alpha;
   float* gamma_cg = p.gamma_c + D.c_off;
@@ -156,6 +156,17 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     __syncthreads();
   }
 
+  // ---- S2 for the first iteration of the launch: Z = H V^{t-1}.  Every
+  //      later Z = H V^t is formed per cell at the end of the previous
+  //      iteration, right after that cell's V update, while its channel
+  //      block is at hand (one staging of each block per iteration).
+  for (int j = 0; j < C; ++j) {
+    float2* Zo = vw.Z[zc] + j * n;
+    block_cgemm_tiled<0>(tile_z, m, n, Nt, cell_h(j), ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
+                         [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
+  }
+  __syncthreads();
+
   const int n_iters = (p.mode == kEvalWsr) ? 1 : p.n_iters;
   double rho = 0.0;
   for (int it = 0; it < n_iters; ++it) {
@@ -163,13 +174,6 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     const float omega = (p.extrapolate && t >= 3) ? (float)(t - 2) / (float)(t + 1) : 0.f;
     float2* Zc = vw.Z[zc];
     float2* Zp = vw.Z[zc ^ 1];
-    // ---- S2: Z = H V^{t-1}
-    for (int j = 0; j < C; ++j) {
-      float2* Zo = Zc + j * n;
-      block_cgemm_tiled<0>(tile_z, m, n, Nt, cell_h(j), ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
-                           [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
-    }
-    __syncthreads();
     // ---- S3a: interference-plus-noise covariance Q_r (upper triangle), sigma^2 = 1
     covariance_phase(D, Ly, [&](int row, int c) { return Zc[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
@@ -202,30 +206,28 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
           for (int a = 0; a < D.Nr; ++a) Zp[(long long)(r * D.Nr + a) * ldz + c] = y[a];
         });
     __syncthreads();
-    // ---- S5: step size per cell, eq. (16)
+    // ---- per cell j, with its channel block staged once: S5 step size
+    //      (eq. (16)), S7 G_j = Htilde_j^H Y_j, Vtilde = Vhat - gamma G over
+    //      V^{t-2}, projection (eq. (15)), then Z_j = Htilde_j V_j^t for the
+    //      next iteration over Y_j's columns (which G_j has consumed)
     const int sflag = s_ctrl[6];
-    for (int k = 0; k < C; ++k) {
-      float gk;
-      if (sflag & 1) {
-        const float2* Hk = cell_h(k);
-        const float lam = lanczos_norm(
-            D, Ly, [&](int i, int q) { return Hk[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, lD, ta, tb,
-            red, &s_bcast);
-        gk = (lam > 0.f) ? 1.f / lam : 0.f;
-        if ((sflag & 2) && tid == 0) gamma_c[k] = gk;
-      } else {
-        gk = (p.gamma_user > 0.f) ? p.gamma_user : gamma_c[k];
-      }
-      if (tid == 0) cellf[k] = gk;
-    }
-    __syncthreads();
-    // ---- S7: G_j = Htilde_j^H Y_j; Vtilde = Vhat - gamma G over V^{t-2}; projection
+    const bool next_z = it + 1 < n_iters;
     for (int j = 0; j < C; ++j) {
-      const float gj = cellf[j];
+      const float2* Hj = cell_h(j);
+      float gj;
+      if (sflag & 1) {
+        const float lam = lanczos_norm(
+            D, Ly, [&](int i, int q) { return Hj[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, lD, ta, tb,
+            red, &s_bcast);
+        gj = (lam > 0.f) ? 1.f / lam : 0.f;
+        if ((sflag & 2) && tid == 0) gamma_c[j] = gj;
+      } else {
+        gj = (p.gamma_user > 0.f) ? p.gamma_user : gamma_c[j];
+      }
       const float2* Vc = vw.V[cur] + (long long)j * Nt * ldv;
       float2* Vn = vw.V[cur ^ 1] + (long long)j * Nt * ldv;
       float nrm = 0.f;
-      block_cgemm_tiled<1>(tile_g, Nt, n, m, cell_h(j), ldh, Zp + j * n, ldz,
+      block_cgemm_tiled<1>(tile_g, Nt, n, m, Hj, ldh, Zp + j * n, ldz,
                            [&](int r, int c, float2 g) {
                              const long long idx = (long long)r * ldv + c;
                              float2 vh = Vc[idx];
@@ -234,18 +236,19 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
                              Vn[idx] = vt;
                              nrm += cabs2(vt);
                            });
-      const double s = block_sum((double)nrm, red);
-      if (tid == 0) cellf[16 + j] = (s > (double)Pc[j]) ? (float)sqrt((double)Pc[j] / s) : 1.f;
-    }
-    __syncthreads();
-    for (int j = 0; j < C; ++j) {
-      const float sj = cellf[16 + j];
+      const double s = block_sum((double)nrm, red);  // block-uniform; all of Vtilde_j written
+      const float sj = (s > (double)Pc[j]) ? (float)sqrt((double)Pc[j] / s) : 1.f;
       if (sj != 1.f) {
-        float2* Vn = vw.V[cur ^ 1] + (long long)j * Nt * ldv;
         for (int e = tid; e < Nt * n; e += blockDim.x) {
           const int r = e / n, c = e - r * n;
           Vn[(long long)r * ldv + c] = cscale(Vn[(long long)r * ldv + c], sj);
         }
+        __syncthreads();
+      }
+      if (next_z) {
+        float2* Zo = Zp + j * n;
+        block_cgemm_tiled<0>(tile_z, m, n, Nt, Hj, ldh, Vn, ldv,
+                             [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
       }
     }
     __syncthreads();

@@ -79,6 +79,33 @@ def test_tc_teacher_forced_step(shape, prec):
     g.close()
 
 
+@pytest.mark.parametrize("shape", [(1, 16, 64, 4, 4), (1, 16, 64, 2, 2), (1, 5, 33, 4, 3)])
+def test_tc_teacher_forced_step_fp32_solves(shape):
+    """BF16X6 GEMMs with the per-user solves in FP32 (fp64_solves = 0; the
+    extrapolation then overlaps the solves on the warps without a user):
+    one step from the oracle's state within 1e-5, 10 iterations."""
+    n, iters = 4, 10
+    insts = small_batch(shape, n, 8500 + sum(shape))
+    opt = osv.Options()
+    runs = [_oracle_states(inst, iters, opt) for inst in insts]
+    g = GpuRun(insts, precision="bf16x6", fp64_solves=0)
+    worst = 0.0
+    for t in range(iters):
+        g.set_state_from_oracle([r[0][t] for r in runs])
+        g.step(1)
+        Vs = g.V()
+        for b in range(n):
+            if t > 0 and runs[b][0][t].stage == 1:
+                relchg = abs(runs[b][2][t].rho - runs[b][2][t - 1].rho) / abs(runs[b][2][t - 1].rho)
+                if abs(relchg - opt.eps1) < 1e-3:
+                    continue
+            e = rel(Vs[b], runs[b][1][t])
+            worst = max(worst, e)
+            assert e <= STEP_TOL["bf16x6"], (shape, b, t + 1, e)
+    print(f"bf16x6 fp32 solves {shape}: teacher-forced worst rel V err {worst:.2e}")
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
 @pytest.mark.parametrize("shape", TC_SHAPES)
 def test_tc_free_running(shape, prec):

@@ -26,7 +26,7 @@ struct WLayout {
 __host__ __device__ inline WLayout plan_wmmse(const InstDesc& D, int budget) {
   WLayout W;
   W.base = plan_layout(D, 0, 1);
-  const int m = W.base.m, n = W.base.n, Nt = D.Nt;
+  const int m = W.base.m, Nt = D.Nt;
   W.lda = pad_ld(Nt);
   int off = align_up(W.base.total, 128);
   W.off_A = off; off += Nt * W.lda * 8;          // A_k

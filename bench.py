@@ -245,13 +245,16 @@ def gap_check(pool, got, oracle_res, name="sweep", iters=None):
     than 1e-5 (oracle.sensitivity; elsewhere they move it by 1e-7 or less)."""
     import numpy as np
     decided = [(b, w) for b, w, mg in oracle_res if mg >= 1e-4]
-    gaps = np.array([abs(got[b] - w) / w for b, w in decided])
+    signed = np.array([(got[b] - w) / w for b, w in decided])
+    gaps = np.abs(signed)
     over = [(b, w, g) for (b, w), g in zip(decided, gaps) if g > 1e-3]
     spreads = pool.map(_spread_worker, [(b, iters or ITERS, w, name) for b, w, _ in over]) if over else []
     return {"checked": len(decided), "near_threshold_skipped": len(oracle_res) - len(decided),
             "max_wsr_gap": float(gaps.max()) if len(gaps) else None,
             "p99_wsr_gap": float(np.percentile(gaps, 99)) if len(gaps) else None,
             "median_wsr_gap": float(np.median(gaps)) if len(gaps) else None,
+            # mean of (GPU - oracle) / oracle: whether the sample leans to one side
+            "mean_signed_wsr_gap": float(signed.mean()) if len(gaps) else None,
             "over_1e-3": len(over), "over_1e-3_fp32_sensitive": int(sum(sp > 1e-5 for sp in spreads)),
             "over_1e-3_unexplained": int(sum(sp <= 1e-5 for sp in spreads)),
             # how far beyond the oracle's own spread the GPU lands on those

@@ -129,7 +129,9 @@ __device__ __forceinline__ float2 zst(Z64 a) { return make_float2((float)a.x, (f
 // Cholesky A = L L^H of an n x n Hermitian matrix (lower triangle of A
 // read); returns false on a non-positive pivot.  iL[j] = 1 / L_jj (one FP64
 // rsqrt per pivot, no division), and the pivots L_jj^2 go to piv[j].
-__device__ bool z_chol(const Z64* A, Z64* L, double* iL, double* piv, int n) {
+template <int n>
+__device__ __forceinline__ bool z_chol(const Z64* A, Z64* L, double* iL, double* piv) {
+#pragma unroll
   for (int j = 0; j < n; ++j) {
     double dj = A[j * n + j].x;
     for (int k = 0; k < j; ++k) dj -= L[j * n + k].x * L[j * n + k].x + L[j * n + k].y * L[j * n + k].y;
@@ -149,7 +151,9 @@ __device__ bool z_chol(const Z64* A, Z64* L, double* iL, double* piv, int n) {
 }
 
 // X = A^{-1} B for A = L L^H (n x n), B n x k, all row-major.
-__device__ void z_chol_solve(const Z64* L, const double* iL, int n, const Z64* B, int k, Z64* X) {
+template <int n, int k>
+__device__ __forceinline__ void z_chol_solve(const Z64* L, const double* iL, const Z64* B, Z64* X) {
+#pragma unroll
   for (int c = 0; c < k; ++c) {
     for (int i = 0; i < n; ++i) {  // L y = b
       Z64 s = B[i * k + c];
@@ -168,8 +172,11 @@ __device__ void z_chol_solve(const Z64* L, const double* iL, int n, const Z64* B
 // T_r = I + Z_r Z_r^H (all columns, FP32, in X.Tc): U_r = T_r^{-1} Z_own (eq. (9), sigma^2 = 1),
 // E_r = I - U_r^H Z_own, W_r = E_r^{-1} (eq. (10); I in stage I), P_r = U_r W_r.
 // Stores T_r^{-1}, U, W, P and log det E_r.  Returns false on a failed factorisation.
-__device__ bool u_solve_user(const UView& X, int r, bool stage2, bool want_ld) {
-  const int Nr = X.Nr, d = X.d, n = X.n;
+// Nr and d are compile-time, so the small matrices live in registers.
+template <int NR, int DD>
+__device__ __noinline__ bool u_solve_user_t(const UView& X, int r, bool stage2, bool want_ld) {
+  constexpr int Nr = NR, d = DD;
+  const int n = X.n;
   Z64 A[16], L[16], I4[16], Ti[16], Zo[16], Uu[16], E[16], Le[16], Wm[16];
   for (int a = 0; a < Nr; ++a)
     for (int b = 0; b < Nr; ++b) {
@@ -177,8 +184,8 @@ __device__ bool u_solve_user(const UView& X, int r, bool stage2, bool want_ld) {
       I4[a * Nr + b] = zmk(a == b ? 1.0 : 0.0, 0.0);
     }
   double iLt[4], pv[4];
-  if (!z_chol(A, L, iLt, pv, Nr)) return false;
-  z_chol_solve(L, iLt, Nr, I4, Nr, Ti);
+  if (!z_chol<Nr>(A, L, iLt, pv)) return false;
+  z_chol_solve<Nr, Nr>(L, iLt, I4, Ti);
   for (int a = 0; a < Nr; ++a)
     for (int s = 0; s < d; ++s) Zo[a * d + s] = zld(X.Z[(r * Nr + a) * n + r * d + s]);
   for (int a = 0; a < Nr; ++a)
@@ -200,11 +207,11 @@ __device__ bool u_solve_user(const UView& X, int r, bool stage2, bool want_ld) {
       E[u * d + s] = zmk(h.x, -h.y);
     }
   double iLe[4], pe[4];
-  if (!z_chol(E, Le, iLe, pe, d)) return false;
+  if (!z_chol<d>(E, Le, iLe, pe)) return false;
   for (int s = 0; s < d; ++s)
     for (int u = 0; u < d; ++u) I4[s * d + u] = zmk(s == u ? 1.0 : 0.0, 0.0);
   if (stage2) {
-    z_chol_solve(Le, iLe, d, I4, d, Wm);
+    z_chol_solve<d, d>(Le, iLe, I4, Wm);
   } else {
     for (int q = 0; q < d * d; ++q) Wm[q] = I4[q];
   }
@@ -223,6 +230,17 @@ __device__ bool u_solve_user(const UView& X, int r, bool stage2, bool want_ld) {
     X.ld[r] = log(prod);
   }
   return true;
+}
+
+// One (N_r, d) pair per instantiation: N_r <= 4, d <= N_r.
+#define AMM_U_PAIRS(F) F(1, 1) F(2, 1) F(2, 2) F(3, 1) F(3, 2) F(3, 3) F(4, 1) F(4, 2) F(4, 3) F(4, 4)
+
+__device__ __forceinline__ bool u_solve_user(const UView& X, int r, bool stage2, bool want_ld) {
+#define AMM_U_SOLVE(a, b) \
+  if (X.Nr == a && X.d == b) return u_solve_user_t<a, b>(X, r, stage2, want_ld);
+  AMM_U_PAIRS(AMM_U_SOLVE)
+#undef AMM_U_SOLVE
+  return false;
 }
 
 // Forward part of iteration t shared by both passes: Z = H Va, the per-user
@@ -377,6 +395,141 @@ __global__ void __launch_bounds__(kUThreads) u_forward_kernel(UParams p) {
   }
 }
 
+// Per-user part of the adjoint of one iteration (thread r < K): Abar =
+// 2 alpha P^H Ybar, Ubar, Pbar and Zhbar = U Abar over the columns, then the
+// adjoints of P = U W, W = E^{-1}, E = I - U^H Zo, U = T^{-1} Zo and
+// T = I + Z Z^H, giving Zbar_r.  N_r and d are compile-time, so the small
+// FP64 matrices live in registers.
+template <int NR, int DD>
+__device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2, const float2* Yb, float2* Zhb,
+                                                 float2* Zb, float2* Ub, float2* Pb) {
+  constexpr int Nr = NR, d = DD;
+  const int n = X.n;
+  const float a2 = 2.f * X.alpha[r];
+  float2 ub[16], pb[16];
+  for (int q = 0; q < Nr * d; ++q) ub[q] = pb[q] = make_float2(0.f, 0.f);
+  const int rot = bank_rot(n);  // lanes hold users: rows r Nr n .. are read with stride Nr n
+  for (int k = 0; k < n; ++k) {
+    const int c = (k + rot < n) ? k + rot : k + rot - n;
+    float2 As[kMaxNr], Ab[kMaxNr];
+    for (int s2 = 0; s2 < d; ++s2) {
+      float2 acc = make_float2(c == r * d + s2 ? -1.f : 0.f, 0.f);
+      float2 acb = make_float2(0.f, 0.f);
+      for (int a = 0; a < Nr; ++a) {
+        acc = cjfma(X.U[(r * Nr + a) * d + s2], X.Zh[(r * Nr + a) * n + c], acc);
+        acb = cjfma(X.P[(r * Nr + a) * d + s2], Yb[(r * Nr + a) * n + c], acb);
+      }
+      As[s2] = acc;
+      Ab[s2] = cscale(acb, a2);
+    }
+    for (int a = 0; a < Nr; ++a) {
+      const float2 zh = X.Zh[(r * Nr + a) * n + c], yb = Yb[(r * Nr + a) * n + c];
+      float2 zhb = make_float2(0.f, 0.f);
+      for (int s2 = 0; s2 < d; ++s2) {
+        // Ubar += Zh Abar^H;  Pbar += 2 alpha Ybar A^H;  Zhbar = U Abar
+        ub[a * d + s2] = cfma(zh, make_float2(Ab[s2].x, -Ab[s2].y), ub[a * d + s2]);
+        pb[a * d + s2] = cfma(cscale(yb, a2), make_float2(As[s2].x, -As[s2].y), pb[a * d + s2]);
+        zhb = cfma(X.U[(r * Nr + a) * d + s2], Ab[s2], zhb);
+      }
+      Zhb[(r * Nr + a) * n + c] = zhb;
+    }
+  }
+  // P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
+  Z64 Ubr[16], Wb[16], Uu[16], Wm[16], Eb[16], Bm[16], Tb[16], Ti[16];
+  for (int q = 0; q < Nr * d; ++q) Uu[q] = zld(X.U[r * Nr * d + q]);
+  for (int q = 0; q < d * d; ++q) Wm[q] = zld(X.W[r * d * d + q]);
+  for (int q = 0; q < Nr * Nr; ++q) Ti[q] = zld(X.Ti[r * Nr * Nr + q]);
+  for (int a = 0; a < Nr; ++a)
+    for (int s2 = 0; s2 < d; ++s2) {
+      Z64 acc = zld(ub[a * d + s2]);
+      for (int u = 0; u < d; ++u) acc = zadd(acc, zmul(zld(pb[a * d + u]), zmk(Wm[s2 * d + u].x, -Wm[s2 * d + u].y)));
+      Ubr[a * d + s2] = acc;
+    }
+  for (int q = 0; q < d * d; ++q) Eb[q] = zmk(0.0, 0.0);
+  if (stage2) {
+    for (int s2 = 0; s2 < d; ++s2)
+      for (int u = 0; u < d; ++u) {
+        Z64 acc = zmk(0.0, 0.0);
+        for (int a = 0; a < Nr; ++a) acc = zadd(acc, zcmul(Uu[a * d + s2], zld(pb[a * d + u])));
+        Wb[s2 * d + u] = acc;
+      }
+    // W = E^{-1}: Ebar = -W^H Wbar W^H  (W Hermitian)
+    Z64 tmp[16];
+    for (int s2 = 0; s2 < d; ++s2)
+      for (int u = 0; u < d; ++u) {
+        Z64 acc = zmk(0.0, 0.0);
+        for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(Wm[s2 * d + v], Wb[v * d + u]));
+        tmp[s2 * d + u] = acc;
+      }
+    for (int s2 = 0; s2 < d; ++s2)
+      for (int u = 0; u < d; ++u) {
+        Z64 acc = zmk(0.0, 0.0);
+        for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(tmp[s2 * d + v], Wm[v * d + u]));
+        Eb[s2 * d + u] = zmk(-acc.x, -acc.y);
+      }
+    // E = I - U^H Zo: Ubar += -Zo Ebar^H
+    for (int a = 0; a < Nr; ++a)
+      for (int s2 = 0; s2 < d; ++s2) {
+        Z64 acc = Ubr[a * d + s2];
+        for (int u = 0; u < d; ++u) {
+          const Z64 zo = zld(X.Z[(r * Nr + a) * n + r * d + u]);
+          acc = zsub(acc, zmul(zo, zmk(Eb[s2 * d + u].x, -Eb[s2 * d + u].y)));
+        }
+        Ubr[a * d + s2] = acc;
+      }
+  }
+  // U = T^{-1} Zo: Bm = T^{-1} Ubar; Zo-bar += Bm; Tbar = -Bm U^H
+  for (int a = 0; a < Nr; ++a)
+    for (int s2 = 0; s2 < d; ++s2) {
+      Z64 acc = zmk(0.0, 0.0);
+      for (int c2 = 0; c2 < Nr; ++c2) acc = zadd(acc, zmul(Ti[a * Nr + c2], Ubr[c2 * d + s2]));
+      Bm[a * d + s2] = acc;
+    }
+  for (int a = 0; a < Nr; ++a)
+    for (int c2 = 0; c2 < Nr; ++c2) {
+      Z64 acc = zmk(0.0, 0.0);
+      for (int s2 = 0; s2 < d; ++s2) acc = zsub(acc, zmul(Bm[a * d + s2], zmk(Uu[c2 * d + s2].x, -Uu[c2 * d + s2].y)));
+      Tb[a * Nr + c2] = acc;
+    }
+  // T = I + Z Z^H: Zbar_r = (Tbar + Tbar^H) Z_r (FP32 over the columns);
+  // own columns also get Bm - U Ebar
+  float2 sym[16], ownb[16];
+  for (int a = 0; a < Nr; ++a)
+    for (int c2 = 0; c2 < Nr; ++c2)
+      sym[a * Nr + c2] = zst(zmk(Tb[a * Nr + c2].x + Tb[c2 * Nr + a].x, Tb[a * Nr + c2].y - Tb[c2 * Nr + a].y));
+  for (int a = 0; a < Nr; ++a)
+    for (int s2 = 0; s2 < d; ++s2) {
+      Z64 acc = Bm[a * d + s2];
+      for (int u = 0; u < d; ++u) acc = zsub(acc, zmul(Uu[a * d + u], Eb[u * d + s2]));
+      ownb[a * d + s2] = zst(acc);
+    }
+  for (int k = 0; k < n; ++k) {
+    const int c = (k + rot < n) ? k + rot : k + rot - n;
+    const bool own = c >= r * d && c < r * d + d;
+    for (int a = 0; a < Nr; ++a) {
+      float2 acc = make_float2(0.f, 0.f);
+      if (own)
+#pragma unroll
+        for (int u = 0; u < d; ++u)
+          if (c - r * d == u) acc = ownb[a * d + u];  // constant index: ownb stays in registers
+      for (int c2 = 0; c2 < Nr; ++c2) acc = cfma(sym[a * Nr + c2], X.Z[(r * Nr + c2) * n + c], acc);
+      Zb[(r * Nr + a) * n + c] = acc;
+    }
+  }
+  for (int q = 0; q < Nr * d; ++q) {
+    Ub[r * Nr * d + q] = zst(Ubr[q]);
+    Pb[r * Nr * d + q] = pb[q];
+  }
+}
+
+__device__ __forceinline__ void u_adjoint_user(const UView& X, int r, bool stage2, const float2* Yb, float2* Zhb,
+                                               float2* Zb, float2* Ub, float2* Pb) {
+#define AMM_U_ADJ(a, b) \
+  if (X.Nr == a && X.d == b) return u_adjoint_user_t<a, b>(X, r, stage2, Yb, Zhb, Zb, Ub, Pb);
+  AMM_U_PAIRS(AMM_U_ADJ)
+#undef AMM_U_ADJ
+}
+
 // Adjoint of one iteration t.  In: A1 = Vbar^t (complete), A2 = the part of
 // Vbar^{t-1} already collected.  Out: A2 += this iteration's share of
 // Vbar^{t-1}, A3 = its share of Vbar^{t-2}, Hb += its share of Hbar,
@@ -425,119 +578,7 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
                        [&](int r, int c, float2 v) { Yb[r * n + c] = cscale(v, -gam); });
   __syncthreads();
   // per user: Abar = 2 alpha P^H Ybar, Ubar, Pbar, Zhbar = U Abar; then W, E and T
-  for (int r = threadIdx.x; r < K; r += blockDim.x) {
-    const float a2 = 2.f * X.alpha[r];
-    float2 ub[16], pb[16];
-    for (int q = 0; q < Nr * d; ++q) ub[q] = pb[q] = make_float2(0.f, 0.f);
-    const int rot = bank_rot(n);  // lanes hold users: rows r Nr n .. are read with stride Nr n
-    for (int k = 0; k < n; ++k) {
-      const int c = (k + rot < n) ? k + rot : k + rot - n;
-      float2 As[kMaxNr], Ab[kMaxNr];
-      for (int s2 = 0; s2 < d; ++s2) {
-        float2 acc = make_float2(c == r * d + s2 ? -1.f : 0.f, 0.f);
-        float2 acb = make_float2(0.f, 0.f);
-        for (int a = 0; a < Nr; ++a) {
-          acc = cjfma(X.U[(r * Nr + a) * d + s2], X.Zh[(r * Nr + a) * n + c], acc);
-          acb = cjfma(X.P[(r * Nr + a) * d + s2], Yb[(r * Nr + a) * n + c], acb);
-        }
-        As[s2] = acc;
-        Ab[s2] = cscale(acb, a2);
-      }
-      for (int a = 0; a < Nr; ++a) {
-        const float2 zh = X.Zh[(r * Nr + a) * n + c], yb = Yb[(r * Nr + a) * n + c];
-        float2 zhb = make_float2(0.f, 0.f);
-        for (int s2 = 0; s2 < d; ++s2) {
-          // Ubar += Zh Abar^H;  Pbar += 2 alpha Ybar A^H;  Zhbar = U Abar
-          ub[a * d + s2] = cfma(zh, make_float2(Ab[s2].x, -Ab[s2].y), ub[a * d + s2]);
-          pb[a * d + s2] = cfma(cscale(yb, a2), make_float2(As[s2].x, -As[s2].y), pb[a * d + s2]);
-          zhb = cfma(X.U[(r * Nr + a) * d + s2], Ab[s2], zhb);
-        }
-        Zhb[(r * Nr + a) * n + c] = zhb;
-      }
-    }
-    // P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
-    Z64 Ubr[16], Wb[16], Uu[16], Wm[16], Eb[16], Bm[16], Tb[16], Ti[16];
-    for (int q = 0; q < Nr * d; ++q) Uu[q] = zld(X.U[r * Nr * d + q]);
-    for (int q = 0; q < d * d; ++q) Wm[q] = zld(X.W[r * d * d + q]);
-    for (int q = 0; q < Nr * Nr; ++q) Ti[q] = zld(X.Ti[r * Nr * Nr + q]);
-    for (int a = 0; a < Nr; ++a)
-      for (int s2 = 0; s2 < d; ++s2) {
-        Z64 acc = zld(ub[a * d + s2]);
-        for (int u = 0; u < d; ++u) acc = zadd(acc, zmul(zld(pb[a * d + u]), zmk(Wm[s2 * d + u].x, -Wm[s2 * d + u].y)));
-        Ubr[a * d + s2] = acc;
-      }
-    for (int q = 0; q < d * d; ++q) Eb[q] = zmk(0.0, 0.0);
-    if (stage2) {
-      for (int s2 = 0; s2 < d; ++s2)
-        for (int u = 0; u < d; ++u) {
-          Z64 acc = zmk(0.0, 0.0);
-          for (int a = 0; a < Nr; ++a) acc = zadd(acc, zcmul(Uu[a * d + s2], zld(pb[a * d + u])));
-          Wb[s2 * d + u] = acc;
-        }
-      // W = E^{-1}: Ebar = -W^H Wbar W^H  (W Hermitian)
-      Z64 tmp[16];
-      for (int s2 = 0; s2 < d; ++s2)
-        for (int u = 0; u < d; ++u) {
-          Z64 acc = zmk(0.0, 0.0);
-          for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(Wm[s2 * d + v], Wb[v * d + u]));
-          tmp[s2 * d + u] = acc;
-        }
-      for (int s2 = 0; s2 < d; ++s2)
-        for (int u = 0; u < d; ++u) {
-          Z64 acc = zmk(0.0, 0.0);
-          for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(tmp[s2 * d + v], Wm[v * d + u]));
-          Eb[s2 * d + u] = zmk(-acc.x, -acc.y);
-        }
-      // E = I - U^H Zo: Ubar += -Zo Ebar^H
-      for (int a = 0; a < Nr; ++a)
-        for (int s2 = 0; s2 < d; ++s2) {
-          Z64 acc = Ubr[a * d + s2];
-          for (int u = 0; u < d; ++u) {
-            const Z64 zo = zld(X.Z[(r * Nr + a) * n + r * d + u]);
-            acc = zsub(acc, zmul(zo, zmk(Eb[s2 * d + u].x, -Eb[s2 * d + u].y)));
-          }
-          Ubr[a * d + s2] = acc;
-        }
-    }
-    // U = T^{-1} Zo: Bm = T^{-1} Ubar; Zo-bar += Bm; Tbar = -Bm U^H
-    for (int a = 0; a < Nr; ++a)
-      for (int s2 = 0; s2 < d; ++s2) {
-        Z64 acc = zmk(0.0, 0.0);
-        for (int c2 = 0; c2 < Nr; ++c2) acc = zadd(acc, zmul(Ti[a * Nr + c2], Ubr[c2 * d + s2]));
-        Bm[a * d + s2] = acc;
-      }
-    for (int a = 0; a < Nr; ++a)
-      for (int c2 = 0; c2 < Nr; ++c2) {
-        Z64 acc = zmk(0.0, 0.0);
-        for (int s2 = 0; s2 < d; ++s2) acc = zsub(acc, zmul(Bm[a * d + s2], zmk(Uu[c2 * d + s2].x, -Uu[c2 * d + s2].y)));
-        Tb[a * Nr + c2] = acc;
-      }
-    // T = I + Z Z^H: Zbar_r = (Tbar + Tbar^H) Z_r (FP32 over the columns);
-    // own columns also get Bm - U Ebar
-    float2 sym[16], ownb[16];
-    for (int a = 0; a < Nr; ++a)
-      for (int c2 = 0; c2 < Nr; ++c2)
-        sym[a * Nr + c2] = zst(zmk(Tb[a * Nr + c2].x + Tb[c2 * Nr + a].x, Tb[a * Nr + c2].y - Tb[c2 * Nr + a].y));
-    for (int a = 0; a < Nr; ++a)
-      for (int s2 = 0; s2 < d; ++s2) {
-        Z64 acc = Bm[a * d + s2];
-        for (int u = 0; u < d; ++u) acc = zsub(acc, zmul(Uu[a * d + u], Eb[u * d + s2]));
-        ownb[a * d + s2] = zst(acc);
-      }
-    for (int k = 0; k < n; ++k) {
-      const int c = (k + rot < n) ? k + rot : k + rot - n;
-      const bool own = c >= r * d && c < r * d + d;
-      for (int a = 0; a < Nr; ++a) {
-        float2 acc = own ? ownb[a * d + (c - r * d)] : make_float2(0.f, 0.f);
-        for (int c2 = 0; c2 < Nr; ++c2) acc = cfma(sym[a * Nr + c2], X.Z[(r * Nr + c2) * n + c], acc);
-        Zb[(r * Nr + a) * n + c] = acc;
-      }
-    }
-    for (int q = 0; q < Nr * d; ++q) {
-      Ub[r * Nr * d + q] = zst(Ubr[q]);
-      Pb[r * Nr * d + q] = pb[q];
-    }
-  }
+  for (int r = threadIdx.x; r < K; r += blockDim.x) u_adjoint_user(X, r, stage2, Yb, Zhb, Zb, Ub, Pb);
   __syncthreads();
   // Hbar += Y Gbar^H + Zhbar Vhat^H + Zbar Va^H  (Gbar = -gam B).  Lanes hold
   // consecutive q, so rows q n of B, Vhat, Va are read with stride n; each

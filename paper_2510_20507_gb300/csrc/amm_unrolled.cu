@@ -253,11 +253,17 @@ __device__ void u_forward_iter(const UView& X, bool stage2, float omega, const f
   for (int e = threadIdx.x; e < Nt * n; e += blockDim.x)
     Vh[e] = make_float2((1.f + omega) * Va[e].x - omega * Vb[e].x, (1.f + omega) * Va[e].y - omega * Vb[e].y);
   __syncthreads();
-  // T_r = I + sum over all columns of z_a conj(z_b), one thread per entry (FP32)
+  // T_r = I + sum over all columns of z_a conj(z_b), one thread per entry (FP32).
+  // Rows of Z are n apart, so each user sweeps the columns from its own
+  // offset (the lanes of one user read the same addresses).
   for (int e = threadIdx.x; e < K * Nr * Nr; e += blockDim.x) {
     const int r = e / (Nr * Nr), ab = e - r * Nr * Nr, a = ab / Nr, b = ab - a * Nr;
+    const int rot = (n & 1) ? 0 : r % n;
     float2 acc = make_float2(a == b ? 1.f : 0.f, 0.f);
-    for (int c = 0; c < n; ++c) acc = cjfma(X.Z[(r * Nr + b) * n + c], X.Z[(r * Nr + a) * n + c], acc);
+    for (int k = 0; k < n; ++k) {
+      const int c = (k + rot < n) ? k + rot : k + rot - n;
+      acc = cjfma(X.Z[(r * Nr + b) * n + c], X.Z[(r * Nr + a) * n + c], acc);
+    }
     X.Tc[e] = acc;
   }
   __syncthreads();

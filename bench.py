@@ -296,8 +296,10 @@ def run_reference(args):
 
 
 def run_e2e(solver, pk, batch, args, dist, dev, world):
-    """The same metric through amm_solve_host: host (pinned) inputs copied in
-    and the WSR copied out inside the timed region."""
+    """The same metric through the host-buffer API: host (pinned) inputs
+    copied in and the WSR copied out inside the timed region.  ``solver``
+    is a Solver (amm_solve_host on one context) or a HostPipeline (one
+    context and stream per part of the batch, copies overlapping solves)."""
     import torch
     Hh = torch.from_numpy(pk.H).pin_memory()
     G0h = torch.from_numpy(pk.G0).pin_memory()
@@ -314,7 +316,7 @@ def run_e2e(solver, pk, batch, args, dist, dev, world):
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist, dev)
     h2d = pk.H.nbytes + pk.G0.nbytes + pk.alpha.nbytes + pk.sigma2.nbytes + pk.P.nbytes
-    return whole_job_rate(world, batch, args.steps, e2e_s), h2d, batch * 8
+    return whole_job_rate(world, batch, args.steps, e2e_s), h2d, batch * 8, wsr_h.numpy().copy()
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -442,9 +444,16 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     # ---- end to end through the C-ABI with host buffers (pinned)
-    e2e_value, h2d, d2h = None, 0, 0
+    e2e_value, h2d, d2h, e2e_single = None, 0, 0, None
     if not args.no_e2e:
-        e2e_value, h2d, d2h = run_e2e(solver, pk, batch, args, dist, dev, world)
+        # HostPipeline: the batch in parts, each on its own context and stream,
+        # so each part's upload overlaps the solves of the others
+        pipe = pkg.HostPipeline(batch, pk.dims[0], chunks=args.e2e_chunks, opts=opts)
+        e2e_value, h2d, d2h, wsr_pipe = run_e2e(pipe, pk, batch, args, dist, dev, world)
+        pipe.close()
+        e2e_single, _, _, wsr_one = run_e2e(solver, pk, batch, args, dist, dev, world)
+        if not np.array_equal(wsr_pipe, wsr_one):  # same instances, same kernels: identical results
+            raise RuntimeError("HostPipeline and amm_solve_host disagree")
     st = torch.empty(batch, dtype=torch.int32, device=dev)
     solver.status(st)
     torch.cuda.synchronize()
@@ -510,7 +519,9 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (H: %.0f MB per GPU)" % (pk.H.nbytes / 1e6)},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "api": f"HostPipeline, {args.e2e_chunks} parts (amm_solve_host per part)",
+                 "single_context": e2e_single}
                 if e2e_value is not None else None),
         "gpu_launches": launches,
         "clocks": clk,
@@ -695,6 +706,8 @@ def main():
     ap.add_argument("--oracle-one-core", type=int, default=32,
                     help="instances of that sample solved again in one process (the one-core figure)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=4,
+                    help="parts of the batch (contexts and streams) of the end-to-end host-buffer leg")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 path alongside")
     ap.add_argument("--fp32-solves", action="store_true",
                     help="run the per-user Hermitian solves in FP32 instead of FP64")

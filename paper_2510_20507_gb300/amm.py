@@ -257,6 +257,55 @@ class Solver:
         return Graph(self, g, (H, alpha, sigma2, P, V0, wsr_out))
 
 
+class HostPipeline:
+    """A host-resident uniform batch solved in ``chunks`` parts, one context
+    and one CUDA stream per part: ``solve_host`` runs amm_solve_host for every
+    part from its own host thread, so the host-to-device copy of one part
+    overlaps the solve of another.  Inputs and outputs are the host buffers
+    of Solver.solve_host for the whole batch (pinned memory, batch-major);
+    results are those of one context over the whole batch, instance by
+    instance."""
+
+    def __init__(self, batch: int, dims, chunks: int = 4, opts: Optional[Opts] = None, **overrides):
+        import concurrent.futures
+        import torch
+        if not isinstance(dims[0], int):
+            raise ValueError("HostPipeline takes one (C, K, Nt, Nr, d) for the whole batch")
+        chunks = max(1, min(int(chunks), batch))
+        edges = [batch * k // chunks for k in range(chunks + 1)]
+        self.parts = [(a, b) for a, b in zip(edges, edges[1:]) if b > a]
+        self.streams = [torch.cuda.Stream() for _ in self.parts]
+        self.solvers = [Solver(b - a, dims, opts, stream=st, **overrides) for (a, b), st in zip(self.parts, self.streams)]
+        s0 = self.solvers[0]
+        nb = self.parts[0][1] - self.parts[0][0]
+        # per-instance sizes of the packed host buffers
+        self.per = {"H": s0.h_elems // nb, "V": s0.v_elems // nb, "u": s0.n_users // nb, "c": s0.n_cells // nb}
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=len(self.parts))
+        self.batch = batch
+
+    def solve_host(self, H, alpha, sigma2, P, V0, n_iters: int, wsr_out, V_out=None):
+        per = self.per
+
+        def run(k):
+            a, b = self.parts[k]
+            self.solvers[k].solve_host(H[a * per["H"]:b * per["H"]], alpha[a * per["u"]:b * per["u"]],
+                                       sigma2[a * per["u"]:b * per["u"]], P[a * per["c"]:b * per["c"]],
+                                       V0[a * per["V"]:b * per["V"]], n_iters, wsr_out[a:b],
+                                       None if V_out is None else V_out[a * per["V"]:b * per["V"]])
+
+        for f in [self.pool.submit(run, k) for k in range(len(self.parts))]:
+            f.result()
+
+    @property
+    def launches(self) -> int:
+        return sum(s.launches for s in self.solvers)
+
+    def close(self):
+        for s in self.solvers:
+            s.close()
+        self.pool.shutdown(wait=True)
+
+
 class Graph:
     """A recorded solve of one Solver (amm_graph_*)."""
 

@@ -264,6 +264,31 @@ def test_solve_host_matches_device_path():
     g.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
+def test_host_pipeline_matches_single_context(prec):
+    """HostPipeline (the batch in parts, one context and stream each, run
+    from concurrent host threads) gives the single-context results bit for
+    bit, V included, for uneven part sizes."""
+    import torch
+    import paper_2510_20507_gb300 as pkg
+    insts = round_inputs(wl.single_cell_64(2, first=0, count=11))
+    pk = wl.pack(insts)
+    host = [torch.from_numpy(x).pin_memory() for x in (pk.H, pk.alpha, pk.sigma2, pk.P, pk.G0)]
+    one = pkg.Solver(len(insts), pk.dims[0], precision=prec)
+    w1 = torch.empty(len(insts), dtype=torch.float64).pin_memory()
+    V1 = torch.empty(one.v_elems, dtype=torch.complex64).pin_memory()
+    one.solve_host(*host, 50, w1, V1)
+    pipe = pkg.HostPipeline(len(insts), pk.dims[0], chunks=3, precision=prec)
+    w2 = torch.zeros(len(insts), dtype=torch.float64).pin_memory()
+    V2 = torch.zeros(one.v_elems, dtype=torch.complex64).pin_memory()
+    pipe.solve_host(*host, 50, w2, V2)
+    assert np.array_equal(w1.numpy(), w2.numpy())
+    assert np.array_equal(V1.numpy(), V2.numpy())
+    assert [b - a for a, b in pipe.parts] == [3, 4, 4]
+    pipe.close()
+    one.close()
+
+
 @pytest.mark.parametrize("shape", [(1, 4, 8, 2, 2), (2, 2, 6, 2, 1), (1, 6, 24, 4, 2)])
 def test_wmmse_step_matches_oracle(shape):
     """amm_wmmse_step (Algorithm 2: eq. (9), eq. (10), eq. (12) with

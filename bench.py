@@ -394,13 +394,17 @@ def run_gpu(args):
     l0 = solver.launches
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with torch.cuda.stream(stream):
         ev0.record(stream)
         for s in range(args.steps):
+            step_ev[s].record(stream)
             one_step(ev_pairs[s])
+        step_ev[args.steps].record(stream)
         ev1.record(stream)
     torch.cuda.synchronize()
     elapsed_ms = ev0.elapsed_time(ev1)
+    step_ms = [a.elapsed_time(b) for a, b in zip(step_ev, step_ev[1:])]
     launches = solver.launches - l0
     # duration of each launch of the iteration kernel, from events on its stream
     iter_ms = [a.elapsed_time(b) for a, b in ev_pairs]
@@ -526,6 +530,9 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "iterate_kernel_ms": avg_iter_ms,
+        # per timed step (CUDA events at the step boundaries, this rank)
+        "ms_per_step_best": min(step_ms),
+        "ms_per_step_median": statistics.median(step_ms),
         "plain_path": plain,
         "speedup_vs_plain": (value / plain["value"]) if plain else None,
         "parity": parity,

@@ -102,6 +102,11 @@ struct UParams {
 // 16 and spread out otherwise.  Odd n needs no offset.
 __device__ __forceinline__ int bank_rot(int n) { return (n & 1) ? 0 : (int)(threadIdx.x & 31) % n; }
 
+// conj(a) b
+__device__ __forceinline__ float2 cjmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+
 struct UView {
   int K, Nt, Nr, d, m, n;
   float2 *H, *Z, *Zh, *Y, *G, *Ti, *Tc, *U, *W, *P;
@@ -440,46 +445,47 @@ __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2
       Zhb[(r * Nr + a) * n + c] = zhb;
     }
   }
-  // P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
-  Z64 Ubr[16], Wb[16], Uu[16], Wm[16], Eb[16], Bm[16], Tb[16], Ti[16];
-  for (int q = 0; q < Nr * d; ++q) Uu[q] = zld(X.U[r * Nr * d + q]);
-  for (int q = 0; q < d * d; ++q) Wm[q] = zld(X.W[r * d * d + q]);
-  for (int q = 0; q < Nr * Nr; ++q) Ti[q] = zld(X.Ti[r * Nr * Nr + q]);
+  // From here FP32: products of the small matrices that the FP64 forward
+  // solve produced (no factorisation).  P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
+  float2 Ubr[16], Wb[16], Uu[16], Wm[16], Eb[16], Bm[16], Tb[16], Ti[16];
+  for (int q = 0; q < Nr * d; ++q) Uu[q] = X.U[r * Nr * d + q];
+  for (int q = 0; q < d * d; ++q) Wm[q] = X.W[r * d * d + q];
+  for (int q = 0; q < Nr * Nr; ++q) Ti[q] = X.Ti[r * Nr * Nr + q];
   for (int a = 0; a < Nr; ++a)
     for (int s2 = 0; s2 < d; ++s2) {
-      Z64 acc = zld(ub[a * d + s2]);
-      for (int u = 0; u < d; ++u) acc = zadd(acc, zmul(zld(pb[a * d + u]), zmk(Wm[s2 * d + u].x, -Wm[s2 * d + u].y)));
+      float2 acc = ub[a * d + s2];
+      for (int u = 0; u < d; ++u) acc = cadd(acc, cmul(pb[a * d + u], make_float2(Wm[s2 * d + u].x, -Wm[s2 * d + u].y)));
       Ubr[a * d + s2] = acc;
     }
-  for (int q = 0; q < d * d; ++q) Eb[q] = zmk(0.0, 0.0);
+  for (int q = 0; q < d * d; ++q) Eb[q] = make_float2(0.f, 0.f);
   if (stage2) {
     for (int s2 = 0; s2 < d; ++s2)
       for (int u = 0; u < d; ++u) {
-        Z64 acc = zmk(0.0, 0.0);
-        for (int a = 0; a < Nr; ++a) acc = zadd(acc, zcmul(Uu[a * d + s2], zld(pb[a * d + u])));
+        float2 acc = make_float2(0.f, 0.f);
+        for (int a = 0; a < Nr; ++a) acc = cadd(acc, cjmul(Uu[a * d + s2], pb[a * d + u]));
         Wb[s2 * d + u] = acc;
       }
     // W = E^{-1}: Ebar = -W^H Wbar W^H  (W Hermitian)
-    Z64 tmp[16];
+    float2 tmp[16];
     for (int s2 = 0; s2 < d; ++s2)
       for (int u = 0; u < d; ++u) {
-        Z64 acc = zmk(0.0, 0.0);
-        for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(Wm[s2 * d + v], Wb[v * d + u]));
+        float2 acc = make_float2(0.f, 0.f);
+        for (int v = 0; v < d; ++v) acc = cadd(acc, cmul(Wm[s2 * d + v], Wb[v * d + u]));
         tmp[s2 * d + u] = acc;
       }
     for (int s2 = 0; s2 < d; ++s2)
       for (int u = 0; u < d; ++u) {
-        Z64 acc = zmk(0.0, 0.0);
-        for (int v = 0; v < d; ++v) acc = zadd(acc, zmul(tmp[s2 * d + v], Wm[v * d + u]));
-        Eb[s2 * d + u] = zmk(-acc.x, -acc.y);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int v = 0; v < d; ++v) acc = cadd(acc, cmul(tmp[s2 * d + v], Wm[v * d + u]));
+        Eb[s2 * d + u] = make_float2(-acc.x, -acc.y);
       }
     // E = I - U^H Zo: Ubar += -Zo Ebar^H
     for (int a = 0; a < Nr; ++a)
       for (int s2 = 0; s2 < d; ++s2) {
-        Z64 acc = Ubr[a * d + s2];
+        float2 acc = Ubr[a * d + s2];
         for (int u = 0; u < d; ++u) {
-          const Z64 zo = zld(X.Z[(r * Nr + a) * n + r * d + u]);
-          acc = zsub(acc, zmul(zo, zmk(Eb[s2 * d + u].x, -Eb[s2 * d + u].y)));
+          const float2 zo = X.Z[(r * Nr + a) * n + r * d + u];
+          acc = csub(acc, cmul(zo, make_float2(Eb[s2 * d + u].x, -Eb[s2 * d + u].y)));
         }
         Ubr[a * d + s2] = acc;
       }
@@ -487,14 +493,14 @@ __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2
   // U = T^{-1} Zo: Bm = T^{-1} Ubar; Zo-bar += Bm; Tbar = -Bm U^H
   for (int a = 0; a < Nr; ++a)
     for (int s2 = 0; s2 < d; ++s2) {
-      Z64 acc = zmk(0.0, 0.0);
-      for (int c2 = 0; c2 < Nr; ++c2) acc = zadd(acc, zmul(Ti[a * Nr + c2], Ubr[c2 * d + s2]));
+      float2 acc = make_float2(0.f, 0.f);
+      for (int c2 = 0; c2 < Nr; ++c2) acc = cadd(acc, cmul(Ti[a * Nr + c2], Ubr[c2 * d + s2]));
       Bm[a * d + s2] = acc;
     }
   for (int a = 0; a < Nr; ++a)
     for (int c2 = 0; c2 < Nr; ++c2) {
-      Z64 acc = zmk(0.0, 0.0);
-      for (int s2 = 0; s2 < d; ++s2) acc = zsub(acc, zmul(Bm[a * d + s2], zmk(Uu[c2 * d + s2].x, -Uu[c2 * d + s2].y)));
+      float2 acc = make_float2(0.f, 0.f);
+      for (int s2 = 0; s2 < d; ++s2) acc = csub(acc, cmul(Bm[a * d + s2], make_float2(Uu[c2 * d + s2].x, -Uu[c2 * d + s2].y)));
       Tb[a * Nr + c2] = acc;
     }
   // T = I + Z Z^H: Zbar_r = (Tbar + Tbar^H) Z_r (FP32 over the columns);
@@ -502,12 +508,12 @@ __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2
   float2 sym[16], ownb[16];
   for (int a = 0; a < Nr; ++a)
     for (int c2 = 0; c2 < Nr; ++c2)
-      sym[a * Nr + c2] = zst(zmk(Tb[a * Nr + c2].x + Tb[c2 * Nr + a].x, Tb[a * Nr + c2].y - Tb[c2 * Nr + a].y));
+      sym[a * Nr + c2] = make_float2(Tb[a * Nr + c2].x + Tb[c2 * Nr + a].x, Tb[a * Nr + c2].y - Tb[c2 * Nr + a].y);
   for (int a = 0; a < Nr; ++a)
     for (int s2 = 0; s2 < d; ++s2) {
-      Z64 acc = Bm[a * d + s2];
-      for (int u = 0; u < d; ++u) acc = zsub(acc, zmul(Uu[a * d + u], Eb[u * d + s2]));
-      ownb[a * d + s2] = zst(acc);
+      float2 acc = Bm[a * d + s2];
+      for (int u = 0; u < d; ++u) acc = csub(acc, cmul(Uu[a * d + u], Eb[u * d + s2]));
+      ownb[a * d + s2] = acc;
     }
   for (int k = 0; k < n; ++k) {
     const int c = (k + rot < n) ? k + rot : k + rot - n;
@@ -523,7 +529,7 @@ __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2
     }
   }
   for (int q = 0; q < Nr * d; ++q) {
-    Ub[r * Nr * d + q] = zst(Ubr[q]);
+    Ub[r * Nr * d + q] = Ubr[q];
     Pb[r * Nr * d + q] = pb[q];
   }
 }
@@ -543,7 +549,7 @@ __device__ __forceinline__ void u_adjoint_user(const UView& X, int r, bool stage
 __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& L, unsigned char* smem, int b, int t,
                                const float2* Va, const float2* Vb, const float2* A1, float2* A2, float2* A3,
                                int* fail) {
-  const int m = X.m, n = X.n, Nt = X.Nt, Nr = X.Nr, d = X.d, K = X.K, N = Nt * n;
+  const int m = X.m, n = X.n, Nt = X.Nt, K = X.K, N = Nt * n;
   double* red = reinterpret_cast<double*>(smem + L.red);
   float2* Vh = reinterpret_cast<float2*>(smem + L.Vh);
   float2* B = reinterpret_cast<float2*>(smem + L.B);

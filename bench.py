@@ -183,30 +183,23 @@ def _instances(name, first, count):
 
 def _oracle_worker(args):
     """Oracle solves of instances [first, first+count) of a workload (the
-    timed sweep unless a name is given): (index, WSR in bits, margin of the
-    stage-I decisions to eps1)."""
+    timed sweep unless a name is given): (index, oracle.parity.Reference:
+    the final WSR in bits of the oracle's trajectory and, where a stage
+    decision came within 1e-4 of eps1, of each other admissible one)."""
     first, count, iters = args[:3]
     name = args[3] if len(args) > 3 else "sweep"
-    from oracle import solvers as osv
-    from oracle import model as om
-    out = []
-    for k, inst in enumerate(_instances(name, first, count)):
-        _round32(inst)
-        V0 = osv.initial_precoder(inst.G0, inst.P)
-        r = osv.ammmse(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0, iters)
-        margin = math.inf
-        for a, b in zip(r.history, r.history[1:]):
-            if a.stage == 1:
-                margin = min(margin, abs(abs(b.rho - a.rho) / abs(a.rho) - 0.1))
-        out.append((first + k, om.wsr_bits(inst.H, r.V, inst.sigma2, inst.alpha, inst.K, inst.Nr, inst.d), margin))
-    return out
+    from oracle import parity as op
+    return [(first + k, op.reference_solves(_round32(inst), iters))
+            for k, inst in enumerate(_instances(name, first, count))]
 
 
-def _spread_worker(args):
-    b, iters, ref = args[:3]
-    name = args[3] if len(args) > 3 else "sweep"
-    from oracle.sensitivity import fp32_spread
-    return fp32_spread(_round32(_instances(name, b, 1)[0]), iters, reference=ref)
+def _judge_worker(args):
+    """oracle.parity.judge of one GPU result beyond the 1e-3 gap (computes
+    the oracle's FP32 spread for it)."""
+    b, got, ref, iters = args[:4]
+    name = args[4] if len(args) > 4 else "sweep"
+    from oracle import parity as op
+    return op.judge(got, ref, _round32(_instances(name, b, 1)[0]), iters)
 
 
 def _oracle_serial(jobs):
@@ -240,26 +233,33 @@ def oracle_throughput(pool, cores, n_instances, offset=0):
 
 def gap_check(pool, got, oracle_res, name="sweep", iters=None):
     """The WSR gap of the GPU's solves to the oracle's on the oracle's
-    sample.  An instance beyond 1e-3 counts as explained when FP32-sized
-    perturbations of the oracle's own arithmetic move its result by more
-    than 1e-5 (oracle.sensitivity; elsewhere they move it by 1e-7 or less)."""
+    sample, every instance judged by oracle.parity: within 1e-3 of the
+    nearest admissible oracle trajectory passes; beyond it, a gap of at most
+    4 x the oracle's own spread under FP32-sized perturbations of its
+    arithmetic passes as FP32-sensitive, anything more fails."""
     import numpy as np
-    decided = [(b, w) for b, w, mg in oracle_res if mg >= 1e-4]
-    signed = np.array([(got[b] - w) / w for b, w in decided])
-    gaps = np.abs(signed)
-    over = [(b, w, g) for (b, w), g in zip(decided, gaps) if g > 1e-3]
-    spreads = pool.map(_spread_worker, [(b, iters or ITERS, w, name) for b, w, _ in over]) if over else []
-    return {"checked": len(decided), "near_threshold_skipped": len(oracle_res) - len(decided),
+    from oracle import parity as op
+    near = [(b, ref) + op.nearest(float(got[b]), ref)[1:] for b, ref in oracle_res]
+    gaps = np.array([g for _, _, g, _ in near])
+    signed = np.array([sg for _, _, _, sg in near])
+    beyond = [(b, ref) for b, ref, g, _ in near if g > op.GAP_TOL]
+    verdicts = (pool.map(_judge_worker, [(b, float(got[b]), ref, iters or ITERS, name) for b, ref in beyond],
+                         chunksize=1) if beyond else [])
+    ratios = [v.gap / max(v.spread, 1e-300) for v in verdicts]
+    failed = sum(not v.ok for v in verdicts)
+    return {"rule": f"gap <= {op.GAP_TOL:g}, else gap <= {op.SPREAD_FACTOR:g} x the oracle's FP32 spread; "
+                    f"stage decisions within {op.SWITCH_MARGIN:g} of eps1 compared with every admissible "
+                    f"trajectory",
+            "checked": len(near), "ambiguous_switch": sum(len(ref.wsr) > 1 for _, ref in oracle_res),
             "max_wsr_gap": float(gaps.max()) if len(gaps) else None,
             "p99_wsr_gap": float(np.percentile(gaps, 99)) if len(gaps) else None,
             "median_wsr_gap": float(np.median(gaps)) if len(gaps) else None,
             # mean of (GPU - oracle) / oracle: whether the sample leans to one side
             "mean_signed_wsr_gap": float(signed.mean()) if len(gaps) else None,
-            "over_1e-3": len(over), "over_1e-3_fp32_sensitive": int(sum(sp > 1e-5 for sp in spreads)),
-            "over_1e-3_unexplained": int(sum(sp <= 1e-5 for sp in spreads)),
-            # how far beyond the oracle's own spread the GPU lands on those
-            "over_1e-3_max_gap_over_spread": (float(max(g / max(sp, 1e-300) for (_, _, g), sp in zip(over, spreads)))
-                                              if over else None)}
+            "within_1e-3": int(np.sum(gaps <= op.GAP_TOL)),
+            "over_1e-3": len(beyond), "over_1e-3_fp32_sensitive": len(verdicts) - failed, "failed": failed,
+            "all_pass": failed == 0,
+            "over_1e-3_max_gap_over_spread": float(max(ratios)) if ratios else None}
 
 
 def run_reference(args):

@@ -136,13 +136,17 @@ def receive_covariance(H, V, sigma2, r, K, Nr, d) -> np.ndarray:
     return T
 
 
-def mmse_receiver(H, V, sigma2, K, Nr, d):
+def mmse_receiver(H, V, sigma2, K, Nr, d, cov_hook=None):
     """U update, eq. (9): U_{i_k} = T^{-1} H_{i_k k} V_{i_k} (eq. (9) writes
-    H_{i_k}; the direct link H_{i_k k} is meant)."""
+    H_{i_k}; the direct link H_{i_k k} is meant).  ``cov_hook``, if given,
+    is applied to each T before the solve (the FP32-sensitivity study of
+    ``oracle.sensitivity`` rounds T there; no solver path sets it)."""
     C = H.shape[0]
     out = []
     for r in users(C, K):
         T = receive_covariance(H, V, sigma2, r, K, Nr, d)
+        if cov_hook is not None:
+            T = cov_hook(T)
         k = cell_of(r, K)
         out.append(np.linalg.solve(T, link(H, r, k, Nr) @ prec(V, r, K, d)))
     return out

@@ -6,7 +6,8 @@ after a fixed number of iterations is a property of a trajectory; at high
 SNR some trajectories amplify rounding, and the oracle itself, perturbed at
 the FP32 level, then ends far from its unperturbed run.  ``fp32_spread``
 measures that, so a free-running FP32 solve can be judged against what FP32
-arithmetic can reproduce at all.
+arithmetic can reproduce at all.  The perturbations enter through the
+explicit hooks of ``solvers.ammmse_iteration``; no module state is changed.
 """
 from __future__ import annotations
 
@@ -16,25 +17,39 @@ from . import model as m
 from . import solvers as s
 
 
-def _perturbed_wsr_bits(inst, iters, cov32, v32, step_rel):
-    exact_cov, exact_step = m.receive_covariance, m.spectral_step
-    if cov32:
-        m.receive_covariance = lambda *a: exact_cov(*a).astype(np.complex64).astype(np.complex128)
-    if step_rel:
-        m.spectral_step = lambda *a: exact_step(*a) * (1.0 + step_rel)
-    try:
-        V0 = s.initial_precoder(inst.G0, inst.P)
-        st = s.AState(V=V0.copy(), Vprev=V0.copy())
-        for _ in range(iters):
-            s.ammmse_iteration(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, st, s.Options())
-            if v32:
-                st.V = st.V.astype(np.complex64).astype(np.complex128)
-        return m.wsr_bits(inst.H, st.V, inst.sigma2, inst.alpha, inst.K, inst.Nr, inst.d)
-    finally:
-        m.receive_covariance, m.spectral_step = exact_cov, exact_step
+def _round_c64(T):
+    return T.astype(np.complex64).astype(np.complex128)
 
 
-def fp32_spread(inst, iters, reference=None):
+def perturbed_wsr_bits(inst, iters, cov32=False, v32=False, step_rel=0.0, opt=None):
+    """Final WSR (bits) of Algorithm 3 (options ``opt``, default the
+    paper's) from the projected V^0, with the receive covariance of eq. (9)
+    rounded to complex64 (cov32), the iterate rounded to complex64 after
+    every iteration (v32) and the spectral step of eq. (16) scaled by
+    1 + step_rel.  With no perturbation this is the plain oracle solve."""
+    cov_hook = _round_c64 if cov32 else None
+    step_hook = (lambda g: g * (1.0 + step_rel)) if step_rel else None
+    opt = opt or s.Options()
+    V0 = s.initial_precoder(inst.G0, inst.P)
+    st = s.AState(V=V0.copy(), Vprev=V0.copy())
+    for _ in range(iters):
+        s.ammmse_iteration(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, st, opt,
+                           cov_hook=cov_hook, step_hook=step_hook)
+        if v32:
+            st.V = _round_c64(st.V)
+    return m.wsr_bits(inst.H, st.V, inst.sigma2, inst.alpha, inst.K, inst.Nr, inst.d)
+
+
+# the perturbations fp32_spread applies: (cov32, v32, step_rel)
+VARIANTS = ((True, False, 0.0), (False, True, 0.0), (False, False, -5e-7), (True, True, 5e-7))
+
+
+def fp32_wsr_samples(inst, iters, opt=None):
+    """The final WSR (bits) under each perturbation of VARIANTS."""
+    return [perturbed_wsr_bits(inst, iters, *v, opt=opt) for v in VARIANTS]
+
+
+def fp32_spread(inst, iters, reference=None, opt=None):
     """Largest relative change of the final WSR (Algorithm 3, default
     options, ``iters`` iterations) under four FP32-sized perturbations: the
     N_r x N_r receive covariance of eq. (9) stored in complex64; the iterate V
@@ -42,12 +57,7 @@ def fp32_spread(inst, iters, reference=None):
     off by -5e-7 relative (the accuracy of an FP32 Lanczos estimate); and the
     first two with a +5e-7 step error together.  Single perturbations can
     cancel by chance on a sensitive instance, hence the maximum.
-    ``reference``: the unperturbed final WSR in bits, if already known."""
-    if reference is None:
-        V0 = s.initial_precoder(inst.G0, inst.P)
-        ref = m.wsr_bits(inst.H, s.ammmse(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0,
-                                          iters).V, inst.sigma2, inst.alpha, inst.K, inst.Nr, inst.d)
-    else:
-        ref = reference
-    variants = [(True, False, 0.0), (False, True, 0.0), (False, False, -5e-7), (True, True, 5e-7)]
-    return max(abs(_perturbed_wsr_bits(inst, iters, *v) - ref) / ref for v in variants)
+    ``reference``: the unperturbed final WSR in bits, if already known;
+    ``opt``: the options of the solve (e.g. a forced switch iteration)."""
+    ref = perturbed_wsr_bits(inst, iters, opt=opt) if reference is None else reference
+    return max(abs(w - ref) / ref for w in fp32_wsr_samples(inst, iters, opt=opt))

@@ -78,26 +78,64 @@ class AState:
     gamma_c: Optional[np.ndarray] = None
 
 
-def ammmse_iteration(H, sigma2, alpha, P, K, Nr, d, st: AState, opt: Options) -> IterRecord:
-    """One pass of the repeat-loop of Algorithm 3, advancing ``st`` in place."""
+# ---- the control flow of Algorithm 3, one decision per function (the
+#      planted-mistake tests replace them one at a time)
+def next_stage(stage: int, t: int, rho: float, rho_prev: Optional[float], opt: Options) -> int:
+    """The stage (1: W = I, 2: W from eq. (10)) of iteration t.  Algorithm 3
+    leaves stage I once the relative WSR change is at most eps1; the test
+    needs R^{t-1}, so it cannot fire at t = 1.  Once in stage II the scheme
+    stays there (reading: the switch latches).  switch_iter >= 1 forces the
+    switch at that iteration instead."""
+    if stage != 1:
+        return stage
+    if opt.switch_iter >= 1:
+        return 2 if t >= opt.switch_iter else 1
+    go = rho_prev is not None and m.relative_change(rho, rho_prev) <= opt.eps1
+    return 2 if go else 1
+
+
+def spectral_step_used(stage_iter: int, t: int, opt: Options) -> bool:
+    """Whether eq. (16) takes gamma = 1/||F_k||_2 in iteration t, the
+    stage_iter-th iteration of the current stage (step_rule 0: the stage's
+    first Tc iterations, the per-stage reading of eq. (16); 1: always;
+    2: never).  The global counter t does not enter the per-stage reading."""
+    return opt.step_rule == 1 or (opt.step_rule == 0 and stage_iter <= opt.Tc)
+
+
+def freezes_gamma_c(stage_iter: int, t: int, opt: Options) -> bool:
+    """Whether the spectral step of this iteration becomes gamma_c, the
+    constant step of eq. (16) for the rest of the stage (step_rule 0: the
+    step of the stage's Tc-th iteration)."""
+    return opt.step_rule == 0 and stage_iter == opt.Tc
+
+
+def tolerance_reached(rho: float, rho_prev: Optional[float], last_stage: int, eps2: float) -> bool:
+    """The stopping test of Algorithm 3: the relative WSR change is at most
+    eps2, checked only after an iteration of the second (weighted) stage."""
+    return last_stage == 2 and rho_prev is not None and m.relative_change(rho, rho_prev) <= eps2
+
+
+def ammmse_iteration(H, sigma2, alpha, P, K, Nr, d, st: AState, opt: Options,
+                     cov_hook=None, step_hook=None) -> IterRecord:
+    """One pass of the repeat-loop of Algorithm 3, advancing ``st`` in place.
+
+    ``cov_hook`` / ``step_hook`` perturb the receive covariance of eq. (9)
+    and the spectral step of eq. (16) for ``oracle.sensitivity``; every
+    solver path leaves them unset."""
     C = H.shape[0]
     t = st.t
     # omega^t, eq. (18); extrapolated point, eq. (17)
     omega = m.extrapolation_weight(t) if opt.extrapolate else 0.0
     Vhat = st.V + omega * (st.V - st.Vprev) if t >= 2 else st.V.copy()
     # U^t by eq. (9)
-    U = m.mmse_receiver(H, Vhat if opt.u_at_extrapolated else st.V, sigma2, K, Nr, d)
+    U = m.mmse_receiver(H, Vhat if opt.u_at_extrapolated else st.V, sigma2, K, Nr, d, cov_hook=cov_hook)
     # R^t: WSR of the current iterate V^{t-1}
     rho = m.wsr(H, st.V, sigma2, alpha, K, Nr, d)
     # stage test of Algorithm 3 (latched)
-    if st.stage == 1:
-        if opt.switch_iter >= 1:
-            go = t >= opt.switch_iter
-        else:
-            go = st.rho_prev is not None and m.relative_change(rho, st.rho_prev) <= opt.eps1
-        if go:
-            st.stage = 2
-            st.stage_iter = 0
+    stage = next_stage(st.stage, t, rho, st.rho_prev, opt)
+    if stage != st.stage:
+        st.stage = stage
+        st.stage_iter = 0
     if st.stage == 2:
         W = m.mse_weight(H, U, st.V, K, Nr, d)             # eq. (10)
     else:
@@ -108,10 +146,11 @@ def ammmse_iteration(H, sigma2, alpha, P, K, Nr, d, st: AState, opt: Options) ->
         st.gamma_c = np.zeros(C)
     gamma = np.zeros(C)
     for k in range(C):
-        spectral = (opt.step_rule == 1) or (opt.step_rule == 0 and st.stage_iter <= opt.Tc)
-        if spectral:
+        if spectral_step_used(st.stage_iter, t, opt):
             gamma[k] = m.spectral_step(H, U, W, alpha, k, K, Nr)
-            if opt.step_rule == 0 and st.stage_iter == opt.Tc:
+            if step_hook is not None:
+                gamma[k] = step_hook(gamma[k])
+            if freezes_gamma_c(st.stage_iter, t, opt):
                 st.gamma_c[k] = gamma[k]
         else:
             gamma[k] = opt.gamma_c if opt.gamma_c > 0 else st.gamma_c[k]
@@ -140,9 +179,9 @@ def ammmse(H, sigma2, alpha, P, K, Nr, d, V0, iters: int,
     hist: List[IterRecord] = []
     converged = False
     for _ in range(iters):
-        if tolerance_stop and hist and hist[-1].stage == 2:
+        if tolerance_stop and hist:
             rho = m.wsr(H, st.V, sigma2, alpha, K, Nr, d)
-            if m.relative_change(rho, st.rho_prev) <= opt.eps2:
+            if tolerance_reached(rho, st.rho_prev, hist[-1].stage, opt.eps2):
                 converged = True
                 break
         hist.append(ammmse_iteration(H, sigma2, alpha, P, K, Nr, d, st, opt))
@@ -207,6 +246,14 @@ class WState:
     rho_prev: Optional[float] = None
 
 
+def mmmse_switch(hist, eps1: float) -> bool:
+    """Whether the MMMSE baseline leaves its W = I stage: the relative
+    change of the last two WSR values (hist holds WSR(V^0), WSR(V^1), ...)
+    is at most eps1; it needs two values, so the first iteration is always
+    an MMSE one."""
+    return len(hist) >= 2 and m.relative_change(hist[-1], hist[-2]) <= eps1
+
+
 def wmmse(H, sigma2, alpha, P, K, Nr, d, V0, iters: int, tol: float = 1e-4,
           max_bisect: int = 100, exact: bool = False, eps: Optional[float] = None,
           mmse_first_stage: bool = False, eps1: float = 0.1):
@@ -224,7 +271,7 @@ def wmmse(H, sigma2, alpha, P, K, Nr, d, V0, iters: int, tol: float = 1e-4,
     it = 0
     for it in range(1, iters + 1):
         U = m.mmse_receiver(H, V, sigma2, K, Nr, d)
-        if stage == 1 and len(hist) >= 2 and m.relative_change(hist[-1], hist[-2]) <= eps1:
+        if stage == 1 and mmmse_switch(hist, eps1):
             stage = 2
         W = m.mse_weight(H, U, V, K, Nr, d) if stage == 2 else m.identity_weights(C, K, d)
         V = np.stack([wmmse_precoder_cell(H, U, W, alpha, P, k, K, Nr, d, tol,

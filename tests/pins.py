@@ -423,3 +423,165 @@ def pin_wmmse_ammmse_agree(n=100, iters=200):
         g = m.spectral_step(inst.H, U, Wt, inst.alpha, 0, 4, 2)
         res = np.linalg.norm(V[0] - m.project(V[0] - g * G[0], inst.P[0])) / np.linalg.norm(V[0])
         assert res <= 1e-5, res
+
+
+# ------------------------------------------------- Algorithm 3 control flow
+def _stage1_wsr_sequence(inst, iters):
+    """WSR(V^t), t = 0..iters, of a run held in stage I (W = I throughout),
+    from the rate definition: R^t of iteration t is entry t - 1."""
+    H, sg, al, P, K, Nr, d = _args(inst)
+    V0 = _V0(inst)
+    pure = s.ammmse(*_args(inst), V0, iters, s.Options(switch_iter=10 ** 9))
+    return pure, [m.wsr(H, V, sg, al, K, Nr, d) for V in [V0] + [h.V for h in pure.history]]
+
+
+def pin_stage_switch_rule(seed=507, iters=14):
+    """Stage test of Algorithm 3: the scheme leaves stage I at the first
+    iteration t >= 2 whose relative WSR change |R^t - R^{t-1}| / R^{t-1} is at
+    most eps1 (R^t = WSR(V^{t-1})), and stays in stage II afterwards.  Checked
+    against WSR values computed from the iterates of a run held in stage I,
+    and against a run whose switch is forced at that iteration (identical
+    iterates).  On this instance the paper's eps1 = 0.1 switches at t = 6 and
+    the first stage-II iterate then raises the WSR by about 13 %, more than
+    eps1, so a switch that is re-tested every iteration would fall back."""
+    inst = _inst(seed, 1, 3, 4, 2, 2)
+    V0 = _V0(inst)
+    pure, R = _stage1_wsr_sequence(inst, iters)
+    for eps1, want in ((0.1, 6), (0.2, 5), (1e9, 2), (0.0, None)):
+        first = next((t for t in range(2, iters + 1) if abs(R[t - 1] - R[t - 2]) <= eps1 * abs(R[t - 2])), None)
+        assert first == want, (eps1, first, want)  # this instance's trajectory, read off by hand
+        run = s.ammmse(*_args(inst), V0, iters, s.Options(eps1=eps1))
+        stages = [h.stage for h in run.history]
+        if want is None:
+            assert stages == [1] * iters, (eps1, stages)
+            forced = pure
+        else:
+            assert stages == [1] * (want - 1) + [2] * (iters - want + 1), (eps1, stages)
+            forced = s.ammmse(*_args(inst), V0, iters, s.Options(switch_iter=want))
+        for a, b in zip(run.history, forced.history):
+            assert np.array_equal(a.V, b.V), eps1
+    # the latch has something to hold here: a stage-II change beyond eps1 = 0.1
+    run = s.ammmse(*_args(inst), V0, iters, s.Options())
+    rho = [h.rho for h in run.history]
+    assert max(abs(b - a) / a for a, b in zip(rho[5:], rho[6:])) > 0.1
+
+
+def pin_step_size_schedule(seed=507, iters=14):
+    """eq. (16) with the per-stage reading: gamma = 1/||F_k||_2 in the first
+    Tc = 3 iterations of each stage, then the last of those values (gamma_c)
+    until the stage ends.  With the switch forced at t = 6 the schedule is
+    spectral at t = 1, 2, 3 and 6, 7, 8, frozen at gamma^3 for t = 4, 5 and at
+    gamma^8 from t = 9 on.  The spectral values are recomputed from each
+    iteration's U (eq. (9) at V^{t-1}) and W; the recorded steps are then
+    shown to be the ones the iterates took, by replaying them through the
+    fixed-step unrolled form."""
+    inst = _inst(seed, 1, 3, 4, 2, 2)
+    H, sg, al, P, K, Nr, d = _args(inst)
+    V0 = _V0(inst)
+    run = s.ammmse(*_args(inst), V0, iters, s.Options(switch_iter=6))
+    kinds = "sssffsssffffff"
+    freeze_src = {4: 3, 5: 3, 9: 8, 10: 8, 11: 8, 12: 8, 13: 8, 14: 8}
+    Vs = [V0] + [h.V for h in run.history]
+    for t, h in enumerate(run.history, 1):
+        assert h.stage == (2 if t >= 6 else 1)
+        if kinds[t - 1] == "s":
+            U = m.mmse_receiver(H, Vs[t - 1], sg, K, Nr, d)
+            W = m.mse_weight(H, U, Vs[t - 1], K, Nr, d) if h.stage == 2 else m.identity_weights(1, K, d)
+            want = m.spectral_step(H, U, W, al, 0, K, Nr)
+        else:
+            want = run.history[freeze_src[t] - 1].gamma[0]
+        assert abs(h.gamma[0] - want) <= 1e-12 * want, (t, h.gamma[0], want)
+    # stage II's frozen step differs from stage I's (W = E^{-1} changes ||F||)
+    assert abs(run.history[8].gamma[0] - run.history[3].gamma[0]) > 1e-3 * run.history[3].gamma[0]
+    Vu, _ = s.ammmse_unrolled(*_args(inst), V0, [h.gamma[0] for h in run.history], switch_iter=6)
+    assert np.allclose(Vu, run.V, rtol=0, atol=1e-12)
+
+
+def pin_tolerance_stop(seed=507, iters=60):
+    """The stopping test of Algorithm 3: the solve ends at the start of the
+    first iteration t that follows a stage-II iteration and sees
+    |R^t - R^{t-1}| <= eps2 R^{t-1}; the result is V^{t-1}.  With eps1 = 0.01
+    (a late switch, at t = 10) and eps2 = 0.05 the stage-I changes drop below
+    eps2 from t = 8 on, where no stop may happen yet."""
+    inst = _inst(seed, 1, 3, 4, 2, 2)
+    H, sg, al, P, K, Nr, d = _args(inst)
+    V0 = _V0(inst)
+    opt = s.Options(eps1=0.01, eps2=0.05)
+    full = s.ammmse(*_args(inst), V0, iters, opt)
+    Vs = [V0] + [h.V for h in full.history]
+    R = [m.wsr(H, V, sg, al, K, Nr, d) for V in Vs]
+    stages = [h.stage for h in full.history]
+    assert stages.index(2) + 1 == 10
+    assert abs(R[7] - R[6]) <= 0.05 * R[6]                # t = 8, still stage I: no stop
+    want = next(t for t in range(2, iters + 1)
+                if stages[t - 2] == 2 and abs(R[t - 1] - R[t - 2]) <= 0.05 * abs(R[t - 2]))
+    tol = s.ammmse(*_args(inst), V0, iters, opt, tolerance_stop=True)
+    assert tol.converged and tol.iters == want - 1, (tol.iters, want)
+    assert np.array_equal(tol.V, Vs[want - 1])
+    # not converged within a budget that ends before that iteration
+    short = s.ammmse(*_args(inst), V0, want - 2, opt, tolerance_stop=True)
+    assert not short.converged and short.iters == want - 2
+
+
+def _feasible_perturbations(rng, V, P, n):
+    for _ in range(n):
+        D = wl.cn01(rng, V.shape)
+        for eps in (1e-2, 1e-4):
+            yield np.stack([m.project(V[k] + eps * D[k], P[k]) for k in range(V.shape[0])])
+
+
+def pin_V_minimizer(seed=94):
+    """eq. (12) (and eq. (20), its W = I case) with exact bisection gives the
+    minimiser of f(U, W, .) over the per-cell power balls: f separates over
+    the cells' precoders, so no feasible perturbation of any cell's block
+    lowers f, whether the power constraint is active (lambda > 0) or not."""
+    rng = np.random.default_rng(seed)
+    seen_active = seen_inactive = False
+    for C, K, Nt, Nr, d, P, W_identity in [(1, 3, 5, 2, 2, 10.0, False), (2, 2, 4, 2, 1, 5.0, False),
+                                           (1, 3, 5, 2, 2, 10.0, True), (1, 3, 4, 2, 2, 1e4, False)]:
+        inst = _inst(seed + C + K + Nt, C, K, Nt, Nr, d, P=P)
+        V = _V0(inst)
+        U = m.mmse_receiver(inst.H, V, inst.sigma2, K, Nr, d)
+        W = m.identity_weights(C, K, d) if W_identity else m.mse_weight(inst.H, U, V, K, Nr, d)
+        res = [s.wmmse_precoder_cell(inst.H, U, W, inst.alpha, inst.P, k, K, Nr, d, exact=True) for k in range(C)]
+        Vs = np.stack([r[0] for r in res])
+        seen_active |= any(r[1] > 0 for r in res)
+        seen_inactive |= any(r[1] == 0 for r in res)
+        for k in range(C):  # feasible: an infeasible point could undercut every feasible one
+            assert float(np.sum(np.abs(Vs[k]) ** 2)) <= inst.P[k] * (1 + 1e-9), (C, K, k)
+        f0 = _objective_at(inst, U, W, Vs)
+        for Vp in _feasible_perturbations(rng, Vs, inst.P, 30):
+            assert _objective_at(inst, U, W, Vp) >= f0 - 1e-10 * max(1.0, abs(f0)), (C, K, W_identity)
+    assert seen_active and seen_inactive
+
+
+def pin_mmmse_first_stage(seed=95, iters=8):
+    """The MMMSE baseline (Algorithm 2 with the mixed warm start): in stage
+    I it is block-coordinate minimisation of the weighted sum-MSE (6) over
+    U (eq. (9)) and V (eq. (20)), so the sum-MSE at (U(V^t), V^t) never
+    increases; with eps1 huge the switch comes at the first test (iteration
+    2), after which the iterates are those of WMMSE started from MMMSE's
+    first iterate."""
+    inst = _inst(seed, 1, 3, 6, 2, 2)
+    H, sg, al, P, K, Nr, d = _args(inst)
+    V0 = _V0(inst)
+    prev = None
+    for t in range(1, iters + 1):
+        Vt, _, _ = s.wmmse(*_args(inst), V0, t, exact=True, mmse_first_stage=True, eps1=0.0)
+        U = m.mmse_receiver(H, Vt, sg, K, Nr, d)
+        f = m.sum_mse(H, U, Vt, sg, al, K, Nr, d)
+        if prev is not None:
+            assert f <= prev + 1e-10 * abs(prev), (t, f, prev)
+        prev = f
+    V1, _, _ = s.wmmse(*_args(inst), V0, 1, exact=True, mmse_first_stage=True, eps1=1e9)
+    Va, ha, _ = s.wmmse(*_args(inst), V0, iters, exact=True, mmse_first_stage=True, eps1=1e9)
+    Vb, hb, _ = s.wmmse(*_args(inst), V1, iters - 1, exact=True)
+    assert np.allclose(Va, Vb, rtol=0, atol=1e-12)
+    assert np.allclose(ha[1:], hb, rtol=1e-13, atol=0)
+    # the first MMSE iterate differs from a WMMSE step (the stage-I update is a different one)
+    Vw, _, _ = s.wmmse(*_args(inst), V0, 1, exact=True)
+    assert np.linalg.norm(V1 - Vw) > 1e-6 * np.linalg.norm(Vw)
+
+
+ALL_PINS += [pin_stage_switch_rule, pin_step_size_schedule, pin_tolerance_stop, pin_V_minimizer,
+             pin_mmmse_first_stage]

@@ -2,11 +2,15 @@
 inputs.
 
 Tolerances.  The GPU's GEMMs and iterate are FP32, its small Hermitian
-solves FP64; the oracle is FP64 throughout.  One projected-gradient step
-from the oracle's own state (teacher forcing) must reproduce the oracle's
-V^t within 1e-5 relative Frobenius error; a free-running solve must end
-within 1e-3 relative WSR of the oracle (the accuracy target of the hot
-path), and the WSR evaluation itself within 1e-6 (FP32 inputs, FP64 log-det).
+solves FP64; the oracle is FP64 throughout.  One iteration from the
+oracle's own state (teacher forcing) must reproduce the oracle's V^t within
+1e-5 relative Frobenius error, as a whole and for every user's block
+(relative to that block or the cell's average block, whichever is larger),
+the WSR R^t it computes within 1e-6, the stage, the stage's iteration count
+and a frozen step gamma_c (1e-5); a free-running solve must end within 1e-3
+relative WSR of the oracle (the accuracy target of the hot path) by the
+rule of oracle.parity; the WSR evaluation itself within 1e-6 (FP32 inputs,
+FP64 log-det).
 """
 import numpy as np
 import pytest
@@ -14,7 +18,8 @@ import pytest
 import workloads as wl
 from oracle import solvers as osv
 
-from gpu_util import GpuRun, check_free_running, oracle_run, oracle_wsr_bits, rel, round_inputs, switch_margin
+from gpu_util import (GpuRun, assert_step_bounds, check_free_running, oracle_run, oracle_wsr_bits, rel,
+                      round_inputs, spawn_pool, teacher_forced)
 
 pytestmark = pytest.mark.gpu
 
@@ -74,49 +79,13 @@ def test_initial_projection(shape):
     g.close()
 
 
-def _oracle_states(inst, iters, opt):
-    """Oracle state before each iteration t = 1..iters, and V^t after it."""
-    V0 = osv.initial_precoder(inst.G0, inst.P)
-    st = osv.AState(V=V0.copy(), Vprev=V0.copy())
-    before, after, recs = [], [], []
-    for _ in range(iters):
-        before.append(osv.AState(V=st.V.copy(), Vprev=st.Vprev.copy(), t=st.t, stage=st.stage,
-                                 stage_iter=st.stage_iter, rho_prev=st.rho_prev,
-                                 gamma_c=None if st.gamma_c is None else st.gamma_c.copy()))
-        recs.append(osv.ammmse_iteration(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d,
-                                         st, opt))
-        after.append(st.V.copy())
-    return before, after, recs
-
-
 @pytest.mark.parametrize("shape", SHAPES)
 def test_teacher_forced_step(shape):
     """Load the oracle's state before iteration t into the GPU, run one
-    iteration, compare V^t (every t of a 12-iteration run: stage I, the
-    switch, spectral and frozen steps, extrapolation)."""
-    n, iters = 6, 12
-    insts = small_batch(shape, n, 3000 + sum(shape))
-    opt = osv.Options()
-    runs = [_oracle_states(inst, iters, opt) for inst in insts]
-    g = GpuRun(insts)
-    worst = 0.0
-    for t in range(iters):
-        states = [r[0][t] for r in runs]
-        g.set_state_from_oracle(states)
-        g.step(1)
-        Vs = g.V()
-        for b in range(n):
-            # skip a step whose stage decision sits within 1e-4 of the threshold
-            rec_prev = runs[b][2][t - 1] if t > 0 else None
-            if rec_prev is not None and states[b].stage == 1:
-                relchg = abs(runs[b][2][t].rho - rec_prev.rho) / abs(rec_prev.rho)
-                if abs(relchg - opt.eps1) < 1e-4:
-                    continue
-            e = rel(Vs[b], runs[b][1][t])
-            worst = max(worst, e)
-            assert e <= STEP_TOL, (shape, b, t + 1, e)
-    g.close()
-    print(f"teacher-forced worst rel err {worst:.2e}")
+    iteration, compare the state after it (every t of a 12-iteration run:
+    stage I, the switch, spectral and frozen steps, extrapolation)."""
+    insts = small_batch(shape, 6, 3000 + sum(shape))
+    assert_step_bounds(teacher_forced(insts, 12), f"teacher-forced {shape}")
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -140,8 +109,7 @@ def test_tiny_fp64_workload_free_running():
     got = g.wsr()
     Vs = g.V()
     g.close()
-    excused = check_free_running(got, insts, 50, "tiny")
-    assert len(excused) <= 2
+    check_free_running(got, insts, 50, "tiny")
     verr = [rel(Vs[b], oracle_run(insts[b], 50).V) for b in range(0, 100, 10)]
     print(f"tiny: median V err {np.median(verr):.2e}")
 
@@ -157,15 +125,9 @@ def test_option_variants(opt):
     g.warmstart()
     g.step(iters)
     got = g.wsr()
-    names = {"tc": "Tc"}
-    oopt = {names.get(k, k): (bool(v) if k == "extrapolate" else v) for k, v in opt.items()}
-    for b, inst in enumerate(insts):
-        ref = oracle_run(inst, iters, **oopt)
-        if "switch_iter" not in opt and switch_margin(ref) < 1e-4:
-            continue
-        want = oracle_wsr_bits(inst, ref.V)
-        assert abs(got[b] - want) <= WSR_TOL * want, (opt, b, got[b], want)
     g.close()
+    oopt = {{"tc": "Tc"}.get(k, k): (bool(v) if k == "extrapolate" else v) for k, v in opt.items()}
+    check_free_running(got, insts, iters, f"option variant {opt}", opt_kw=oopt)
 
 
 def test_single_cell_64_full_batch_sampled():
@@ -238,9 +200,9 @@ def test_solve_tolerance_mode():
         V0 = osv.initial_precoder(inst.G0, inst.P)
         ref = osv.ammmse(inst.H, inst.sigma2, inst.alpha, inst.P, 4, 2, 2, V0, 200, tolerance_stop=True)
         rhos = [h.rho for h in ref.history]
-        near = any(abs(abs(y - x) / x - 1e-3) < 1e-6 for x, y in zip(rhos, rhos[1:]))
-        if near or switch_margin(ref) < 1e-4:
-            continue
+        # no stage or stopping decision of these instances lies near its threshold
+        assert all(abs(abs(y - x) / x - 1e-3) >= 1e-6 and abs(abs(y - x) / x - 0.1) >= 1e-4
+                   for x, y in zip(rhos, rhos[1:])), b
         assert it[b] == ref.iters, (b, it[b], ref.iters)
         assert st[b] == (0 if ref.converged else 6)
         want = oracle_wsr_bits(inst, ref.V)
@@ -315,27 +277,8 @@ def test_teacher_forced_step_fp32_solves(shape):
     """fp64_solves = 0: the per-user Cholesky solves in FP32 (log-det from
     log1p of the pivots of I + M computed from M) still reproduce the
     oracle's step within 1e-5."""
-    n, iters = 4, 10
-    insts = small_batch(shape, n, 8000 + sum(shape))
-    opt = osv.Options()
-    runs = [_oracle_states(inst, iters, opt) for inst in insts]
-    g = GpuRun(insts, fp64_solves=0)
-    worst = 0.0
-    for t in range(iters):
-        states = [r[0][t] for r in runs]
-        g.set_state_from_oracle(states)
-        g.step(1)
-        Vs = g.V()
-        for b in range(n):
-            if t > 0 and states[b].stage == 1:
-                relchg = abs(runs[b][2][t].rho - runs[b][2][t - 1].rho) / abs(runs[b][2][t - 1].rho)
-                if abs(relchg - opt.eps1) < 1e-4:
-                    continue
-            e = rel(Vs[b], runs[b][1][t])
-            worst = max(worst, e)
-            assert e <= STEP_TOL, (shape, b, t + 1, e)
-    print(f"fp32 solves {shape}: teacher-forced worst rel err {worst:.2e}")
-    g.close()
+    insts = small_batch(shape, 4, 8000 + sum(shape))
+    assert_step_bounds(teacher_forced(insts, 10, gpu_opts=dict(fp64_solves=0)), f"fp32 solves {shape}")
 
 
 def test_contexts_of_different_sizes_coexist():
@@ -354,34 +297,6 @@ def test_contexts_of_different_sizes_coexist():
     b.close()
 
 
-def _teacher_forced_errors(insts, iters, picks, gpu_opts=None, **opts):
-    """Worst relative V^t error of one GPU iteration started from the
-    oracle's state, over iterations 1..iters of the given instances (opts:
-    options both sides take under the same name; gpu_opts: GPU only)."""
-    runs = {b: _oracle_states(insts[b], iters, osv.Options(**opts)) for b in picks}
-    g = GpuRun(insts, **opts, **(gpu_opts or {}))
-    worst = 0.0
-    for t in range(iters):
-        states = []
-        for b, inst in enumerate(insts):
-            if b in runs:
-                states.append(runs[b][0][t])
-            else:  # instances not checked keep a valid state
-                V0 = osv.initial_precoder(inst.G0, inst.P)
-                states.append(osv.AState(V=V0, Vprev=V0.copy()))
-        g.set_state_from_oracle(states)
-        g.step(1)
-        Vs = g.V()
-        for b in picks:
-            if t > 0 and runs[b][0][t].stage == 1:
-                relchg = abs(runs[b][2][t].rho - runs[b][2][t - 1].rho) / abs(runs[b][2][t - 1].rho)
-                if abs(relchg - 0.1) < 1e-4:
-                    continue
-            worst = max(worst, rel(Vs[b], runs[b][1][t]))
-    g.close()
-    return worst
-
-
 def test_uneven_batch_per_step():
     """An uneven batch (Nt in 16..256, K in 4..64, Nr in {1, 2, 4},
     d = min(Nr, 2), P = 0..30 dB) in one launch, blocks ordered longest
@@ -391,42 +306,46 @@ def test_uneven_batch_per_step():
     cost = [i.K * i.K * i.Nr * i.Nt * i.d for i in insts]
     order = np.argsort(cost)
     picks = [int(order[0]), int(order[1]), int(order[len(order) // 2]), 183, int(order[-1])]
-    worst = _teacher_forced_errors(insts, 6, picks)
-    print(f"uneven: teacher-forced worst rel err {worst:.2e}")
-    assert worst <= STEP_TOL
+    assert_step_bounds(teacher_forced(insts, 6, picks), "uneven")
 
 
 def test_seven_cell_layout_per_step():
     """Seven hexagonal cells (Nt=128, K=10, Nr=2, d=2, path loss and
-    shadowing, -104 dBm noise, 46 dBm per BS): the multi-cell path with H,
-    V and Z in global memory, channels normalised by the noise level inside
-    amm_set_problem.  One iteration from the oracle's state matches it."""
-    insts = round_inputs(wl.hex7(n=256, count=6))
-    worst = _teacher_forced_errors(insts, 8, [0, 3])
-    print(f"seven cells: teacher-forced worst rel err {worst:.2e}")
-    assert worst <= STEP_TOL
+    shadowing, -104 dBm noise, 46 dBm per BS): all 50 iterations of 16
+    instances, each started from the oracle's state, match it per step (V,
+    every user's block, R^t, stage, gamma_c).  Channels are normalised by
+    the noise level inside amm_set_problem."""
+    insts = round_inputs(wl.hex7(n=256, count=16))
+    with spawn_pool() as pool:
+        assert_step_bounds(teacher_forced(insts, 50, pool=pool), "seven cells, 50 iterations")
 
 
-def _free_running_sampled(insts, iters, sample, label):
+def _free_running(insts, iters):
     g = GpuRun(insts)
     g.warmstart()
     g.step(iters)
     got = g.wsr()
     assert np.all(g.status() == 0)
     g.close()
-    check_free_running(got, insts, iters, label, sample=sample)
+    return got
 
 
 def test_uneven_batch_free_running():
-    insts = round_inputs(wl.uneven(n=4096, count=192))
-    cost = [i.K * i.K * i.Nr * i.Nt * i.d for i in insts]
-    order = np.argsort(cost)
-    sample = [int(b) for b in order[:4]] + [int(order[len(order) // 2]), 183, int(order[-1])]
-    _free_running_sampled(insts, 30, sample, "uneven")
+    """The whole uneven batch (4096 instances, 30 iterations) in one launch;
+    every 32nd instance (128, the bench's oracle sample) judged."""
+    insts = round_inputs(wl.uneven(n=4096))
+    got = _free_running(insts, 30)
+    with spawn_pool() as pool:
+        check_free_running(got, insts, 30, "uneven", sample=range(0, 4096, 32), pool=pool)
 
 
 def test_seven_cell_free_running():
-    _free_running_sampled(round_inputs(wl.hex7(n=256, count=24)), 50, [0, 17], "seven cells")
+    """The whole seven-cell batch (256 instances, 50 iterations), every
+    instance judged."""
+    insts = round_inputs(wl.hex7(n=256))
+    got = _free_running(insts, 50)
+    with spawn_pool() as pool:
+        check_free_running(got, insts, 50, "seven cells", pool=pool)
 
 
 @pytest.mark.parametrize("shape", [(1, 48, 16, 2, 2), (1, 8, 256, 1, 1), (1, 35, 256, 1, 1), (1, 64, 256, 2, 2),
@@ -438,9 +357,7 @@ def test_spectral_step_every_iteration(shape):
     rank(F_k) is far below Nt, and where the top of the spectrum is dense
     (K d = 128 of Nt = 256)."""
     insts = small_batch(shape, 3, 7000 + sum(shape))
-    worst = _teacher_forced_errors(insts, 8, [0, 1, 2], step_rule=1)
-    print(f"spectral every iteration {shape}: teacher-forced worst rel err {worst:.2e}")
-    assert worst <= STEP_TOL
+    assert_step_bounds(teacher_forced(insts, 8, step_rule=1), f"spectral every iteration {shape}")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
@@ -450,6 +367,4 @@ def test_timed_workload_high_snr_per_step(prec):
     instances whose free-running trajectories are FP32-sensitive too."""
     picks = [100, 5488, 5570, 6495, 6992]
     sub = round_inputs([wl.single_cell_64(first=b, count=1)[0] for b in picks])
-    worst = _teacher_forced_errors(sub, 50, list(range(len(sub))), gpu_opts=dict(precision=prec))
-    print(f"timed workload {prec}: teacher-forced worst rel err over 50 iterations {worst:.2e}")
-    assert worst <= STEP_TOL
+    assert_step_bounds(teacher_forced(sub, 50, gpu_opts=dict(precision=prec)), f"timed workload {prec}")

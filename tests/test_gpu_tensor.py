@@ -12,9 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import solvers as osv
-
-from gpu_util import GpuRun, check_free_running, rel, round_inputs
+from gpu_util import GpuRun, assert_step_bounds, check_free_running, round_inputs, teacher_forced
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +25,9 @@ TC_SHAPES = [
     (1, 1, 5, 1, 1),
 ]
 STEP_TOL = {"bf16x6": 1e-5, "bf16x3": 2e-4, "bf16": 2e-2}
+RHO_TOL = {"bf16x6": 1e-6, "bf16x3": 2e-5, "bf16": 2e-3}
+GAMMA_TOL = {"bf16x6": 1e-5, "bf16x3": 2e-4, "bf16": 2e-2}
+FLIP = {"bf16x6": 1e-4, "bf16x3": 1e-3, "bf16": 1e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -40,43 +41,16 @@ def small_batch(shape, n, seed):
     return round_inputs([wl.random_small(rng, *shape) for _ in range(n)])
 
 
-def _oracle_states(inst, iters, opt):
-    V0 = osv.initial_precoder(inst.G0, inst.P)
-    st = osv.AState(V=V0.copy(), Vprev=V0.copy())
-    before, after, recs = [], [], []
-    for _ in range(iters):
-        before.append(osv.AState(V=st.V.copy(), Vprev=st.Vprev.copy(), t=st.t, stage=st.stage,
-                                 stage_iter=st.stage_iter, rho_prev=st.rho_prev,
-                                 gamma_c=None if st.gamma_c is None else st.gamma_c.copy()))
-        recs.append(osv.ammmse_iteration(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d,
-                                         st, opt))
-        after.append(st.V.copy())
-    return before, after, recs
-
-
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
 @pytest.mark.parametrize("shape", TC_SHAPES)
 def test_tc_teacher_forced_step(shape, prec):
-    n, iters = 4, 10
-    insts = small_batch(shape, n, 5000 + sum(shape))
-    opt = osv.Options()
-    runs = [_oracle_states(inst, iters, opt) for inst in insts]
-    g = GpuRun(insts, precision=prec)
-    worst = 0.0
-    for t in range(iters):
-        g.set_state_from_oracle([r[0][t] for r in runs])
-        g.step(1)
-        Vs = g.V()
-        for b in range(n):
-            if t > 0 and runs[b][0][t].stage == 1:
-                relchg = abs(runs[b][2][t].rho - runs[b][2][t - 1].rho) / abs(runs[b][2][t - 1].rho)
-                if abs(relchg - opt.eps1) < 1e-3:
-                    continue
-            e = rel(Vs[b], runs[b][1][t])
-            worst = max(worst, e)
-            assert e <= STEP_TOL[prec], (shape, prec, b, t + 1, e)
-    print(f"{prec} {shape}: teacher-forced worst rel V err {worst:.2e}")
-    g.close()
+    """One iteration from the oracle's state, every t of a 10-iteration
+    run: V (whole and per user block), R^t, stage and gamma_c, with the
+    precision's bounds (R^t and gamma_c scale with the GEMM error)."""
+    insts = small_batch(shape, 4, 5000 + sum(shape))
+    worst = teacher_forced(insts, 10, gpu_opts=dict(precision=prec), flip_margin=FLIP[prec])
+    assert_step_bounds(worst, f"{prec} {shape}", v_tol=STEP_TOL[prec], rho_tol=RHO_TOL[prec],
+                       gamma_tol=GAMMA_TOL[prec])
 
 
 @pytest.mark.parametrize("shape", [(1, 16, 64, 4, 4), (1, 16, 64, 2, 2), (1, 5, 33, 4, 3)])
@@ -84,26 +58,9 @@ def test_tc_teacher_forced_step_fp32_solves(shape):
     """BF16X6 GEMMs with the per-user solves in FP32 (fp64_solves = 0; the
     extrapolation then overlaps the solves on the warps without a user):
     one step from the oracle's state within 1e-5, 10 iterations."""
-    n, iters = 4, 10
-    insts = small_batch(shape, n, 8500 + sum(shape))
-    opt = osv.Options()
-    runs = [_oracle_states(inst, iters, opt) for inst in insts]
-    g = GpuRun(insts, precision="bf16x6", fp64_solves=0)
-    worst = 0.0
-    for t in range(iters):
-        g.set_state_from_oracle([r[0][t] for r in runs])
-        g.step(1)
-        Vs = g.V()
-        for b in range(n):
-            if t > 0 and runs[b][0][t].stage == 1:
-                relchg = abs(runs[b][2][t].rho - runs[b][2][t - 1].rho) / abs(runs[b][2][t - 1].rho)
-                if abs(relchg - opt.eps1) < 1e-3:
-                    continue
-            e = rel(Vs[b], runs[b][1][t])
-            worst = max(worst, e)
-            assert e <= STEP_TOL["bf16x6"], (shape, b, t + 1, e)
-    print(f"bf16x6 fp32 solves {shape}: teacher-forced worst rel V err {worst:.2e}")
-    g.close()
+    insts = small_batch(shape, 4, 8500 + sum(shape))
+    worst = teacher_forced(insts, 10, gpu_opts=dict(precision="bf16x6", fp64_solves=0))
+    assert_step_bounds(worst, f"bf16x6 fp32 solves {shape}")
 
 
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])

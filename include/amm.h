@@ -226,11 +226,15 @@ AMM_API amm_status amm_solve_host(amm_ctx* ctx, const void* H, const float* alph
  * in one static device array of 32 MiB that every GPU loading the library
  * holds until the process exits; batches needing more get AMM_EINVAL with
  * the byte count in `err` (a caller buffer of err_len bytes, may be NULL).
- * opts may be NULL; its precision must be AMM_FP32.
+ * opts may be NULL; it is checked as amm_create checks it (AMM_EINVAL /
+ * AMM_EUNSUPPORTED), and its precision must be AMM_FP32 (AMM_EUNSUPPORTED
+ * otherwise).
  *
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call reuses the array and overwrites or clears what it
+ * device, with that device current) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not call
+ * this entry point on a device after cudaDeviceReset (the reset destroys the
+ * context holding the array, so the kept address is stale).  Every call reuses the array and overwrites or clears what it
  * reads, so consecutive calls are independent; calls whose GPU work overlaps
  * (two host threads, or two streams) race on the array and must not be
  * issued.  Asynchronous on `stream` (a cudaStream_t; NULL = legacy default
@@ -239,6 +243,14 @@ AMM_API amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const amm_
                                      const float* alpha, const float* sigma2, const float* P, const void* V0,
                                      int n_iters, void* V_out, double* wsr_out, void* stream, char* err,
                                      int err_len);
+
+/* Fault injection for tests, on the host: the nth device allocation that
+ * amm_create or amm_solve_host makes from now on (nth = 1: the next one)
+ * fails as if the device were out of memory, without calling cudaMalloc, so
+ * the AMM_ENOMEM paths and their clean-up can be exercised with no GPU
+ * fault.  nth <= 0 disarms it.  Process-wide; not for production use.
+ * (No counterpart in the paper.) */
+AMM_API void amm_test_fail_alloc(int nth);
 
 /* Release the context and its workspace (synchronises its stream). */
 AMM_API void amm_destroy(amm_ctx* ctx);

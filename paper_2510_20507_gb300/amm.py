@@ -48,7 +48,7 @@ class State(ctypes.Structure):
 EXPORTS = ["amm_default_opts", "amm_create", "amm_sizes", "amm_set_problem", "amm_warmstart", "amm_step",
            "amm_solve", "amm_wsr", "amm_wmmse_step", "amm_get_V", "amm_get_state", "amm_set_state",
            "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count",
-           "amm_solve_noalloc", "amm_graph_create", "amm_graph_launch", "amm_graph_destroy", "amm_unrolled_create", "amm_unrolled_forward", "amm_unrolled_backward",
+           "amm_solve_noalloc", "amm_test_fail_alloc", "amm_graph_create", "amm_graph_launch", "amm_graph_destroy", "amm_unrolled_create", "amm_unrolled_forward", "amm_unrolled_backward",
            "amm_unrolled_status", "amm_unrolled_last_error", "amm_unrolled_destroy"]
 
 _lib = None
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "amm_launch_count": (i64, [vp]),
         "amm_solve_noalloc": (i32, [i32, ctypes.POINTER(Dims), ctypes.POINTER(Opts), vp, vp, vp, vp, vp, i32, vp,
                                     vp, vp, ctypes.c_char_p, i32]),
+        "amm_test_fail_alloc": (None, [i32]),
         "amm_graph_create": (i32, [vp, vp, vp, vp, vp, vp, i32, vp, ctypes.POINTER(vp)]),
         "amm_graph_launch": (i32, [vp]),
         "amm_graph_destroy": (None, [vp]),
@@ -344,6 +345,7 @@ class UnrolledSolver:
         self.h = h
         self.batch, self.dims, self.T = batch, tuple(dims), T
         self._keep = None
+        self.generation = 0  # forward calls so far: which call the stored checkpoints belong to
 
     def _check(self, st: int):
         if st != AMM_OK:
@@ -362,6 +364,7 @@ class UnrolledSolver:
 
     def forward(self, H, alpha, sigma2, P, V0, gamma, wsr_out):
         self._keep = (H, alpha, sigma2, P, V0, gamma)  # read again by backward
+        self.generation += 1
         self._check(self.lib.amm_unrolled_forward(self.h, _ptr(H), _ptr(alpha), _ptr(sigma2), _ptr(P), _ptr(V0),
                                                   _ptr(gamma), _ptr(wsr_out)))
         return wsr_out

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <numeric>
 #include <string>
@@ -146,10 +147,19 @@ static bool dims_ok(const amm_dims& d, std::string* why) {
   return true;
 }
 
+// Injected allocation failures (amm_test_fail_alloc): the n-th device
+// allocation from now on fails as if the device were out of memory.
+static std::atomic<int> g_fail_alloc_in{0};
+
 template <class T>
 static cudaError_t dalloc(T** p, long long count) {
   *p = nullptr;
   if (count <= 0) count = 1;
+  // an injected failure: counted down per allocation, fires at zero (no CUDA call)
+  int left = g_fail_alloc_in.load();
+  while (left > 0 && !g_fail_alloc_in.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left == 1) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), (size_t)count * sizeof(T));
 }
 
@@ -160,6 +170,25 @@ static void free_all(amm_ctx* c) {
     if (q) cudaFree(q);
 }
 
+namespace amm {
+// Option checks shared by every entry point that takes an amm_opts
+// (amm_create, amm_solve_noalloc): AMM_OK, or the status and a message.
+amm_status check_opts(const amm_opts& o, const char** why) {
+  if (o.precision != AMM_FP32 && o.precision != AMM_BF16 && o.precision != AMM_BF16X3 && o.precision != AMM_BF16X6)
+    return *why = "unknown precision", AMM_EINVAL;
+  if (o.u_at_extrapolated) return *why = "u_at_extrapolated = 1 is not implemented", AMM_EUNSUPPORTED;
+  if (o.step_rule < 0 || o.step_rule > 2 || o.tc < 0 || !(o.eps1 >= 0) || !(o.eps2 >= 0))
+    return *why = "bad step_rule / tc / eps (step_rule in [0, 2], tc >= 0, eps1 >= 0, eps2 >= 0)", AMM_EINVAL;
+  if ((o.step_rule == 2 || (o.step_rule == 0 && o.tc == 0)) && !(o.gamma_c > 0))
+    return *why = "a fixed step needs gamma_c > 0", AMM_EINVAL;
+  if (o.lanczos_steps < 1 || o.lanczos_steps > kMaxLanczos) return *why = "lanczos_steps must be in [1, 64]", AMM_EINVAL;
+  if (o.gemm_tile < 0 || o.gemm_tile > 3) return *why = "gemm_tile must be in [0, 3]", AMM_EINVAL;
+  return AMM_OK;
+}
+}  // namespace amm
+
+extern "C" void amm_test_fail_alloc(int nth) { g_fail_alloc_in.store(nth > 0 ? nth : 0); }
+
 extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims, int n_dims, const amm_opts* opts,
                                  void* stream) {
   if (!out) return fail(nullptr, AMM_EINVAL, "out is NULL");
@@ -169,16 +198,11 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
   amm_opts o;
   amm_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision != AMM_FP32 && o.precision != AMM_BF16 && o.precision != AMM_BF16X3 && o.precision != AMM_BF16X6)
-    return fail(nullptr, AMM_EINVAL, "unknown precision");
-  if (o.u_at_extrapolated) return fail(nullptr, AMM_EUNSUPPORTED, "u_at_extrapolated = 1 is not implemented");
-  if (o.step_rule < 0 || o.step_rule > 2 || o.tc < 0 || !(o.eps1 >= 0) || !(o.eps2 >= 0))
-    return fail(nullptr, AMM_EINVAL, "bad step_rule / tc / eps");
-  if ((o.step_rule == 2 || (o.step_rule == 0 && o.tc == 0)) && !(o.gamma_c > 0))
-    return fail(nullptr, AMM_EINVAL, "a fixed step needs gamma_c > 0");
-  if (o.lanczos_steps < 1 || o.lanczos_steps > amm::kMaxLanczos)
-    return fail(nullptr, AMM_EINVAL, "lanczos_steps must be in [1, 64]");
-  if (o.gemm_tile < 0 || o.gemm_tile > 3) return fail(nullptr, AMM_EINVAL, "gemm_tile must be in [0, 3]");
+  {
+    const char* why = nullptr;
+    const amm_status st = amm::check_opts(o, &why);
+    if (st != AMM_OK) return fail(nullptr, st, why);
+  }
   if (o.spin_budget < 1) o.spin_budget = 2000000000ll;
 
   amm_ctx* c = new (std::nothrow) amm_ctx();

@@ -32,6 +32,7 @@ __global__ void init_kernel(const InstDesc* desc, const float2* V0, const float*
                             Scalars* sc, float* gamma_c, int switch_iter);
 cudaError_t iterate_set_smem(int bytes);
 void iterate_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p);
+amm_status check_opts(const amm_opts& o, const char** why);
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
 constexpr int kNoAllocMaxDevices = 64;
@@ -40,6 +41,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of the array, looked up once per device with that device
 // current (in host code the array's name is only a host-side stand-in).
+// The address is cached for the life of the process: a cudaDeviceReset
+// destroys the context the array lives in, after which the cached address
+// is stale, so this entry point must not be used on a device after
+// cudaDeviceReset has been called on it.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[kNoAllocMaxDevices];
 
@@ -94,12 +99,18 @@ extern "C" amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const a
   amm_opts o;
   amm_default_opts(&o);
   if (opts) o = *opts;
+  {
+    // the same option checks as amm_create, then what this entry point adds
+    const char* why = nullptr;
+    const amm_status st = check_opts(o, &why);
+    if (st != AMM_OK) {
+      char msg[200];
+      snprintf(msg, sizeof msg, "amm_solve_noalloc: %s", why);
+      return noalloc_fail(err, err_len, st, msg);
+    }
+  }
   if (o.precision != AMM_FP32)
-    return noalloc_fail(err, err_len, AMM_EINVAL, "amm_solve_noalloc: only the FP32 GEMM path (AMM_FP32)");
-  if (o.u_at_extrapolated || o.step_rule < 0 || o.step_rule > 2 || o.tc < 0 ||
-      ((o.step_rule == 2 || (o.step_rule == 0 && o.tc == 0)) && !(o.gamma_c > 0)) || o.lanczos_steps < 1 ||
-      o.lanczos_steps > kMaxLanczos || o.gemm_tile < 0 || o.gemm_tile > 3)
-    return noalloc_fail(err, err_len, AMM_EINVAL, "amm_solve_noalloc: unsupported option combination");
+    return noalloc_fail(err, err_len, AMM_EUNSUPPORTED, "amm_solve_noalloc: only the FP32 GEMM path (AMM_FP32)");
   const amm_dims& d = dims[0];
   if (d.cells < 1 || d.cells > kMaxCells || d.users < 1 || d.nt < 1 || d.nt > 4096 || d.nr < 1 ||
       d.nr > kMaxNr || d.d < 1 || d.d > d.nr || (long long)d.cells * d.users * d.nr > 4096 ||

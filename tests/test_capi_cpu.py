@@ -98,3 +98,41 @@ def test_binding_fails_loudly_without_library(tmp_path):
             b.load_library(str(tmp_path / "missing.so"))
     finally:
         b._lib = saved
+
+
+def test_injected_allocation_failure_gives_enomem(lib):
+    """A device allocation failure inside amm_create (injected on the host:
+    the first allocation fails, no CUDA call is made) is reported as
+    AMM_ENOMEM with no context returned."""
+    import paper_2510_20507_gb300 as pkg
+    lib.amm_test_fail_alloc(1)
+    try:
+        st, h = _create(lib, 4, [(1, 4, 8, 2, 2)])
+    finally:
+        lib.amm_test_fail_alloc(0)
+    assert st == pkg.AMM_ENOMEM and not h.value
+    assert b"allocation" in lib.amm_last_error(None)
+
+
+def _noalloc(lib, **opts):
+    import paper_2510_20507_gb300 as pkg
+    o = pkg.default_opts(**opts)
+    d = pkg.amm.Dims(1, 4, 8, 2, 2)
+    err = ctypes.create_string_buffer(256)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the options are rejected first
+    st = lib.amm_solve_noalloc(4, ctypes.byref(d), ctypes.byref(o), fake, fake, fake, fake, fake, 10, fake, fake,
+                               None, err, len(err))
+    return st, err.value
+
+
+def test_noalloc_checks_options_like_create(lib):
+    import paper_2510_20507_gb300 as pkg
+    assert _noalloc(lib, eps1=float("nan"))[0] == pkg.AMM_EINVAL
+    assert _noalloc(lib, eps1=-0.1)[0] == pkg.AMM_EINVAL
+    assert _noalloc(lib, eps2=float("nan"))[0] == pkg.AMM_EINVAL
+    assert _noalloc(lib, step_rule=2)[0] == pkg.AMM_EINVAL          # fixed step without gamma_c
+    assert _noalloc(lib, precision=9)[0] == pkg.AMM_EINVAL
+    st, msg = _noalloc(lib, u_at_extrapolated=1)
+    assert st == pkg.AMM_EUNSUPPORTED and b"u_at_extrapolated" in msg
+    st, msg = _noalloc(lib, precision="bf16x6")
+    assert st == pkg.AMM_EUNSUPPORTED and b"FP32" in msg

@@ -6,6 +6,7 @@ the call must return normally, and the device must stay usable for a
 fresh context whose solves match the FP64 oracle."""
 import numpy as np
 import pytest
+import torch
 
 import workloads as wl
 
@@ -40,3 +41,31 @@ def test_wait_budget_exhausted_reports_timeout(prec):
         want = oracle_wsr_bits(inst, oracle_run(inst, 10).V)
         assert abs(got[b] - want) <= 1e-4 * want
     ok.close()
+
+
+@pytest.mark.parametrize("nth", [1, 3, 7])
+def test_injected_allocation_failure_cleans_up(nth):
+    """A device allocation that fails part-way through amm_create (injected
+    on the host at the nth allocation) returns AMM_ENOMEM after freeing what
+    it had allocated; the device is untouched and a context created next
+    solves correctly."""
+    import ctypes
+    import paper_2510_20507_gb300 as pkg
+    lib = pkg.load_library()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    lib.amm_test_fail_alloc(nth)
+    try:
+        with pytest.raises(pkg.AmmError) as ei:
+            pkg.Solver(64, (1, 16, 64, 4, 4))
+    finally:
+        lib.amm_test_fail_alloc(0)
+    assert ei.value.status == pkg.AMM_ENOMEM
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (2 << 20)  # nothing of the failed context stays allocated
+    insts = wl.tiny_fp64(3)
+    g = GpuRun(insts)
+    g.warmstart()
+    g.step(5)
+    assert np.all(np.isfinite(g.wsr())) and np.all(g.status() == 0)
+    g.close()

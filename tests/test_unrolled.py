@@ -216,3 +216,47 @@ def test_gpu_unrolled_config_nt64_k16_t20():
     assert np.allclose(g.grad.cpu().numpy(), out["gamma_bar"].sum(0), rtol=1e-5, atol=1e-6)
     assert np.allclose(H.grad.cpu().numpy(), out["H_bar"], rtol=1e-5, atol=1e-6)
     solver.close()
+
+
+@pytest.mark.gpu
+def test_gpu_unrolled_two_forwards_then_backward():
+    """Two graphs on one solver (e.g. two losses, or a validation pass in
+    between): the backward of the first, taken after the second forward,
+    gives the gradients of a lone forward/backward of the first; an in-place
+    edit of H after a forward is refused by torch's version check."""
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2510_20507_gb300 as pkg
+    from gpu_util import to_dev
+    from paper_2510_20507_gb300.unrolled import unrolled_wsr
+    T, ck, sw = 6, 3, 3
+    insts = _rounded([_instance((1, 3, 6, 2, 2), 900 + b) for b in range(4)])
+    gam = _gammas(insts[0], T).astype(np.float32)
+
+    def args(scale):
+        H = to_dev((scale * np.stack([i.H[0] for i in insts])).astype(np.complex64)).requires_grad_(True)
+        al = to_dev(np.stack([i.alpha for i in insts]).astype(np.float32))
+        s2 = to_dev(np.stack([i.sigma2 for i in insts]).astype(np.float32))
+        P = to_dev(np.array([i.P[0] for i in insts], dtype=np.float32))
+        V0 = to_dev(np.stack([osv.initial_precoder(i.G0, i.P)[0] for i in insts]).astype(np.complex64))
+        g = to_dev(gam.copy()).requires_grad_(True)
+        return H, g, al, s2, P, V0
+
+    solver = pkg.UnrolledSolver(len(insts), (1, 3, 6, 2, 2), T, ckpt_every=ck, switch_iter=sw)
+    a = args(1.0)
+    unrolled_wsr(solver, a[0], a[1], *a[2:]).sum().backward()
+    want_H, want_g = a[0].grad.clone(), a[1].grad.clone()
+    b, c = args(1.0), args(1.3)
+    lb = unrolled_wsr(solver, b[0], b[1], *b[2:]).sum()
+    lc = unrolled_wsr(solver, c[0], c[1], *c[2:]).sum()   # a second forward on the same solver
+    lb.backward()
+    assert torch.equal(b[0].grad, want_H) and torch.equal(b[1].grad, want_g)
+    lc.backward()
+    assert not torch.equal(c[0].grad, want_H)
+    d = args(1.0)
+    ld = unrolled_wsr(solver, d[0], d[1], *d[2:]).sum()
+    with torch.no_grad():
+        d[0].mul_(2.0)
+    with pytest.raises(RuntimeError):
+        ld.backward()
+    solver.close()

@@ -35,6 +35,8 @@ ITERS = 50
 N_PER_P = 1024
 HEX7_N, HEX7_ITERS = 256, 50
 UNEVEN_N, UNEVEN_ITERS = 4096, 30
+SOLVES = {"fp64": 1, "ff": 2, "fp32": 0}
+SOLVE_NAMES = {"fp64": "f64", "ff": "f32x2 (float-float, about 48-bit significands)", "fp32": "f32"}
 WORKLOAD = "single-cell P sweep: Nt=64, K=16, Nr=4, d=4, iid CN(0,1), P=0..30 dB (7x1024 instances), 50 iterations"
 
 
@@ -355,7 +357,7 @@ def run_gpu(args):
     batch = len(insts)
     C, K, Nt, Nr, d = pk.dims[0]
     stream = torch.cuda.Stream(device=dev)
-    opts = pkg.default_opts(precision=args.precision, fp64_solves=0 if args.fp32_solves else 1)
+    opts = pkg.default_opts(precision=args.precision, fp64_solves=SOLVES[args.solves])
     if args.smem_budget:
         opts.smem_budget = args.smem_budget
     solver = pkg.Solver(batch, pk.dims[0], opts=opts, stream=stream)
@@ -519,7 +521,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances_per_gpu": batch, "iterations": ITERS,
-                   "precision": args.precision, "small_solves": "f32" if args.fp32_solves else "f64",
+                   "precision": args.precision, "small_solves": SOLVE_NAMES[args.solves],
                    "l2": "inputs larger than L2 (H: %.0f MB per GPU)" % (pk.H.nbytes / 1e6)},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -578,12 +580,15 @@ def run_unrolled(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         step()
     e1.record()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     # roofline: algorithmic flops of a forward + adjoint step = per iteration
     # the two forward GEMMs (Z = H V, G = H^H Y) and the two adjoint products
@@ -603,7 +608,7 @@ def run_unrolled(args):
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "unrolled: Nt=64, K=16, Nr=2, d=2, P=20 dB, T=20, checkpoints every 5, "
                                              "stage II from iteration 4", "instances": n},
-                      "roofline": roof}))
+                      "roofline": roof, "clocks": clk}))
     solver.close()
     return 0
 
@@ -636,7 +641,7 @@ def run_other(args):
     dims = pk.dims[0] if pk.uniform else pk.dims
     prec = args.precision if args.precision != "bf16x6" else "fp32"  # tensor-core path: single cell, Nt <= 64 only
     dev = torch.device("cuda", 0)
-    s = pkg.Solver(len(insts), dims, precision=prec, fp64_solves=0 if args.fp32_solves else 1)
+    s = pkg.Solver(len(insts), dims, precision=prec, fp64_solves=SOLVES[args.solves])
     H, G0 = torch.from_numpy(pk.H).to(dev), torch.from_numpy(pk.G0).to(dev)
     al, s2, P = (torch.from_numpy(x).to(dev) for x in (pk.alpha, pk.sigma2, pk.P))
     wsr = torch.empty(len(insts), dtype=torch.float64, device=dev)
@@ -650,12 +655,15 @@ def run_other(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         step()
     e1.record()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     got = wsr.cpu().numpy()
     st = torch.empty(len(insts), dtype=torch.int32, device=dev)
@@ -690,7 +698,7 @@ def run_other(args):
                       "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": prec, "data": "synthetic",
                       "config": {"workload": desc, "iterations": iters}, "roofline": roof, "cpu_baseline": cpu,
-                      "parity": parity}))
+                      "parity": parity, "clocks": clk}))
     return 0
 
 
@@ -718,11 +726,15 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 path alongside")
     ap.add_argument("--fp32-solves", action="store_true",
                     help="run the per-user Hermitian solves in FP32 instead of FP64")
+    ap.add_argument("--solves", default=None, choices=["fp64", "ff", "fp32"],
+                    help="arithmetic of the per-user Hermitian solves (default fp64; ff = float-float pairs)")
     ap.add_argument("--instances", type=int, default=0,
                     help="solve an evenly spread subset of the batch (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.solves is None:
+        args.solves = "fp32" if args.fp32_solves else "fp64"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "unrolled":

@@ -101,19 +101,32 @@ typedef struct {
                            the instance gets AMM_ETIMEOUT; 2e9 (about 1 s) */
   int smem_budget;      /* bytes of shared memory per block the solver may use;
                            0 = automatic */
-  int fp64_solves;      /* 1: the per-user Nr x Nr / d x d Cholesky solves of the U
-                           and W updates run in FP64 (default); 0: in FP32.  The
-                           WSR evaluation of amm_wsr is FP64 either way. */
+  int fp64_solves;      /* arithmetic of the per-user Nr x Nr / d x d Cholesky
+                           solves of the U and W updates (eqs. (9), (10)):
+                           1: FP64 (default); 2: float-float (pairs of FP32,
+                           about 48 significant bits, on the FP32 pipe: a
+                           cheaper stand-in for FP64, rates from FP32 log1p);
+                           0: FP32.  The WSR evaluation of amm_wsr is FP64
+                           whatever this says.  Other values: AMM_EINVAL. */
   int gemm_tile;        /* register tile of the FP32-path block GEMMs: 0 automatic
                            (by instance size), 1: 4x4, 2: 2x2, 3: 4x2 (set by
                            the autotuner); 0 */
+  int cluster_cells;    /* multi-cell instances (2 <= cells <= 8) whose channel does
+                           not fit one block's shared memory, on the FP32 GEMM path:
+                           1 = one thread-block cluster per instance, one block per
+                           cell, each keeping its cell's channel block resident and
+                           exchanging the per-user covariance parts and U, W over
+                           distributed shared memory (default, when such a cluster
+                           fits the GPU); 0 = one block per instance, one cell's
+                           channel block staged per cell and iteration */
 } amm_opts;
 
 typedef struct amm_ctx amm_ctx;
 
 /* Fill *opts with the defaults: eps1 0.1, eps2 1e-3, tc 3, gamma_c 0,
  * extrapolate 1, switch_iter -1, step_rule 0, AMM_FP32, u_at_extrapolated 0,
- * lanczos_steps 64, spin_budget 2e9, smem_budget 0, fp64_solves 1, gemm_tile 0. */
+ * lanczos_steps 64, spin_budget 2e9, smem_budget 0, fp64_solves 1, gemm_tile 0,
+ * cluster_cells 1. */
 AMM_API void amm_default_opts(amm_opts* opts);
 
 /* Create a solver for `batch` instances.  `dims` points to `n_dims` entries:
@@ -261,6 +274,13 @@ AMM_API const char* amm_last_error(const amm_ctx* ctx);
 
 /* Number of kernel launches this context has issued, for launch accounting. */
 AMM_API int64_t amm_launch_count(const amm_ctx* ctx);
+
+/* Which iteration kernel the context runs (chosen in amm_create from the
+ * sizes and options): 0 one block per instance with CUDA-core FP32 GEMMs,
+ * 1 one block per instance with tcgen05 GEMMs, 2 one thread-block cluster per
+ * multi-cell instance (see cluster_cells); -1 for a NULL context.  (No
+ * counterpart in the paper.) */
+AMM_API int amm_path(const amm_ctx* ctx);
 
 /* ---------------------------------------------------------------------
  * CUDA graph of a whole solve.

@@ -15,10 +15,11 @@ oracle number the wrong reference for some instances:
   iteration (``reference_solves``), each the oracle's solve with that switch
   forced, and the GPU result is compared with the nearest.
 * At high SNR some trajectories amplify rounding: the oracle itself, with
-  FP32-sized perturbations of its own arithmetic, moves by ``spread``
-  (``oracle.sensitivity.fp32_spread``).  An instance beyond GAP_TOL passes
-  as FP32-sensitive only if its gap is at most SPREAD_FACTOR times that
-  spread; otherwise it fails.
+  perturbations of the size of the FP32 iteration's per-step error, moves by
+  ``spread`` (``oracle.sensitivity.fp32_spread``).  An instance beyond
+  GAP_TOL passes as FP32-sensitive only if its gap is at most SPREAD_FACTOR
+  times that spread; otherwise it fails.  (The spread is computed only as
+  far as the verdict needs: it stops once it reaches gap / SPREAD_FACTOR.)
 """
 from __future__ import annotations
 
@@ -128,7 +129,7 @@ def judge(gpu_wsr: float, ref: Reference, inst=None, iters: int = 0, opt: Option
         o = opt or s.Options()
         if ref.switch[k] is not None or k > 0:
             o = dataclasses.replace(o, switch_iter=10 ** 9 if ref.switch[k] is None else ref.switch[k])
-        spread = fp32_spread(inst, iters, reference=ref.wsr[k], opt=o)
+        spread = fp32_spread(inst, iters, reference=ref.wsr[k], opt=o, stop_at=gap / SPREAD_FACTOR)
     v.spread = spread
     v.sensitive = gap <= SPREAD_FACTOR * spread
     v.ok = v.sensitive

@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
                 ("gamma_c", ctypes.c_double), ("extrapolate", ctypes.c_int), ("switch_iter", ctypes.c_int),
                 ("step_rule", ctypes.c_int), ("precision", ctypes.c_int), ("u_at_extrapolated", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
-                ("smem_budget", ctypes.c_int), ("fp64_solves", ctypes.c_int), ("gemm_tile", ctypes.c_int)]
+                ("smem_budget", ctypes.c_int), ("fp64_solves", ctypes.c_int), ("gemm_tile", ctypes.c_int),
+                ("cluster_cells", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -47,7 +48,7 @@ class State(ctypes.Structure):
 
 EXPORTS = ["amm_default_opts", "amm_create", "amm_sizes", "amm_set_problem", "amm_warmstart", "amm_step",
            "amm_solve", "amm_wsr", "amm_wmmse_step", "amm_get_V", "amm_get_state", "amm_set_state",
-           "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count",
+           "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count", "amm_path",
            "amm_solve_noalloc", "amm_test_fail_alloc", "amm_graph_create", "amm_graph_launch", "amm_graph_destroy", "amm_unrolled_create", "amm_unrolled_forward", "amm_unrolled_backward",
            "amm_unrolled_status", "amm_unrolled_last_error", "amm_unrolled_destroy"]
 
@@ -83,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "amm_destroy": (None, [vp]),
         "amm_last_error": (ctypes.c_char_p, [vp]),
         "amm_launch_count": (i64, [vp]),
+        "amm_path": (i32, [vp]),
         "amm_solve_noalloc": (i32, [i32, ctypes.POINTER(Dims), ctypes.POINTER(Opts), vp, vp, vp, vp, vp, i32, vp,
                                     vp, vp, ctypes.c_char_p, i32]),
         "amm_test_fail_alloc": (None, [i32]),
@@ -248,6 +250,13 @@ class Solver:
     @property
     def launches(self) -> int:
         return int(self.lib.amm_launch_count(self.h))
+
+    @property
+    def path(self) -> str:
+        """The iteration kernel this context runs: "block" (CUDA-core GEMMs),
+        "tensor" (tcgen05 GEMMs) or "cluster" (one cluster per multi-cell
+        instance)."""
+        return {0: "block", 1: "tensor", 2: "cluster"}[int(self.lib.amm_path(self.h))]
 
     def capture(self, H, alpha, sigma2, P, V0, n_iters: int, wsr_out) -> "Graph":
         """Record set_problem + warmstart + step(n_iters) + wsr as a CUDA graph

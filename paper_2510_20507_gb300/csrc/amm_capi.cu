@@ -17,16 +17,20 @@
 
 namespace amm {
 cudaError_t iterate_set_smem(int bytes);
-void iterate_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p);
+void iterate_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p);
 __global__ void normalize_kernel(const InstDesc* desc, const float2* Hin, const float* alpha, const float* sigma2,
                                  const float* P, float2* Hout, Scalars* sc);
 __global__ void init_kernel(const InstDesc* desc, const float2* V0, const float* P, float2* V, float2* Vprev,
                             Scalars* sc, float* gamma_c, int switch_iter);
 cudaError_t tc_set_smem(int bytes);
-void tc_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p, int prec);
+void tc_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p, int prec);
 __global__ void wmmse_kernel(IterParams p, float bisect_tol, int bisect_max);
 int wmmse_plan_bytes(const InstDesc* desc, int batch, int budget);
 int tc_plan_bytes(const InstDesc* desc, int batch, int budget, int lanczos_steps, int prec);
+int cluster_plan_bytes(const InstDesc* desc, int batch, int budget, int lanczos_steps);
+cudaError_t cluster_set_smem(int bytes);
+cudaError_t cluster_max_active(int C, int smem, int* out);
+cudaError_t cluster_launch(int solves, int batch, int C, int smem, cudaStream_t st, const IterParams& p);
 
 // Gather / scatter of the per-instance scalars for amm_get_state / amm_set_state.
 __global__ void get_scalars_kernel(const Scalars* sc, int n, int* t, int* stage, int* stage_iter, double* rho_prev,
@@ -85,6 +89,7 @@ struct amm_ctx {
   int smem_bytes = 0;
   int tc_bytes = 0;  // shared memory of the tensor-core kernel (0: plain path)
   int wm_bytes = 0;  // shared memory of the WMMSE kernel (-1: sizes it does not cover)
+  int cl_bytes = 0;  // shared memory per block of the cluster kernel (0: not used)
   bool problem_set = false;
   bool started = false;
   std::string err;
@@ -109,6 +114,12 @@ static amm_status check_launch(amm_ctx* ctx, const char* what) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, what);
   return AMM_OK;
 }
+// the same check for a launch already counted
+static amm_status check_launch_counted(amm_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  return AMM_OK;
+}
 
 extern "C" void amm_default_opts(amm_opts* o) {
   if (!o) return;
@@ -126,6 +137,8 @@ extern "C" void amm_default_opts(amm_opts* o) {
   o->spin_budget = 2000000000ll;  // SM clock cycles, about one second
   o->smem_budget = 0;
   o->fp64_solves = 1;
+  o->gemm_tile = 0;
+  o->cluster_cells = 1;
 }
 
 static bool dims_ok(const amm_dims& d, std::string* why) {
@@ -183,6 +196,7 @@ amm_status check_opts(const amm_opts& o, const char** why) {
     return *why = "a fixed step needs gamma_c > 0", AMM_EINVAL;
   if (o.lanczos_steps < 1 || o.lanczos_steps > kMaxLanczos) return *why = "lanczos_steps must be in [1, 64]", AMM_EINVAL;
   if (o.gemm_tile < 0 || o.gemm_tile > 3) return *why = "gemm_tile must be in [0, 3]", AMM_EINVAL;
+  if (o.fp64_solves < 0 || o.fp64_solves > 2) return *why = "fp64_solves must be 0, 1 or 2", AMM_EINVAL;
   return AMM_OK;
 }
 }  // namespace amm
@@ -295,6 +309,18 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
       return fail(nullptr, AMM_ECUDA, std::string("set-up failed: ") + cudaGetErrorString(e));
     }
   }
+  if (o.precision == AMM_FP32 && o.cluster_cells && C0 >= 2) {
+    // one cluster per instance where some instance's channel does not fit one block
+    bool restaged = false;
+    for (int b = 0; b < batch && !restaged; ++b)
+      restaged = amm::plan_layout(c->hdesc[b], budget, o.lanczos_steps).off_H < 0;
+    const int clb = restaged ? amm::cluster_plan_bytes(c->hdesc.data(), batch, budget, o.lanczos_steps) : -1;
+    int active = 0;
+    if (clb > 0 && amm::cluster_set_smem(amm::kSmemMax - 1024) == cudaSuccess &&
+        amm::cluster_max_active(C0, clb, &active) == cudaSuccess && active >= 1)
+      c->cl_bytes = clb;
+    cudaGetLastError();  // a cluster that does not fit leaves the plain kernel in charge
+  }
   if ((e = cudaMemcpy(c->ddesc, c->hdesc.data(), sizeof(InstDesc) * batch, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(Scalars) * batch)) ||
       // the limit is per kernel, not per context: raise it to the largest budget any
@@ -377,12 +403,19 @@ static amm::IterParams base_params(amm_ctx* c) {
 }
 
 static amm_status launch_iterate(amm_ctx* c, const amm::IterParams& p) {
-  const bool f64 = c->opts.fp64_solves != 0 || p.mode == amm::kEvalWsr;  // the WSR is always FP64
+  // 0 FP32, 1 FP64, 2 float-float solves; the final WSR evaluation is always FP64
+  const int solves = (p.mode == amm::kEvalWsr) ? 1 : c->opts.fp64_solves;
+  if (c->cl_bytes > 0) {
+    c->launches += 1;
+    const cudaError_t e = amm::cluster_launch(solves, c->batch, c->C, c->cl_bytes, c->stream, p);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cluster_iterate_kernel");
+    return check_launch_counted(c, "cluster_iterate_kernel");
+  }
   if (c->tc_bytes > 0 && p.mode != amm::kEvalWsr) {
-    amm::tc_launch(f64, c->batch, c->tc_bytes, c->stream, p, c->opts.precision);
+    amm::tc_launch(solves, c->batch, c->tc_bytes, c->stream, p, c->opts.precision);
     return check_launch(c, "tc_iterate_kernel");
   }
-  amm::iterate_launch(f64, c->batch, c->smem_bytes, c->stream, p);
+  amm::iterate_launch(solves, c->batch, c->smem_bytes, c->stream, p);
   return check_launch(c, "iterate_kernel");
 }
 
@@ -536,6 +569,12 @@ extern "C" const char* amm_last_error(const amm_ctx* c) {
 }
 
 extern "C" int64_t amm_launch_count(const amm_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" int amm_path(const amm_ctx* c) {
+  if (!c) return -1;
+  if (c->cl_bytes > 0) return 2;
+  return c->tc_bytes > 0 ? 1 : 0;
+}
 
 // ---------------------------------------------------------------- CUDA graph
 struct amm_graph {

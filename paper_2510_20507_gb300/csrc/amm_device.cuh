@@ -5,6 +5,9 @@
 
 #include <math.h>
 
+#include <type_traits>
+
+#include "amm_ff.cuh"
 #include "amm_internal.cuh"
 
 namespace amm {
@@ -374,7 +377,71 @@ static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, b
   return false;
 }
 
-// FP64 per-user solve by eight lanes: lane (c, p) of the group works on the
+// Arithmetic of the eight-lane per-user solve: FP64 (double) or
+// float-float (ff, amm_ff.cuh) behind one interface, so both run the same
+// sequence of operations.  flip(v, f) = f ? -v : v; positive(v): v > 0 and
+// finite; Lg: the type the log-determinant terms are summed in.
+template <class R>
+struct PairArith;
+
+template <>
+struct PairArith<double> {
+  typedef double R;
+  typedef double Lg;
+  static __device__ __forceinline__ R fma(R a, R b, R c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ R mul(R a, R b) { return a * b; }
+  static __device__ __forceinline__ R add(R a, R b) { return a + b; }
+  static __device__ __forceinline__ R neg(R a) { return -a; }
+  static __device__ __forceinline__ R flip(R v, bool f) {  // on the sign bit: no FP64 instruction
+    return __longlong_as_double(__double_as_longlong(v) ^ (f ? (long long)0x8000000000000000ull : 0ll));
+  }
+  static __device__ __forceinline__ R shfl(R v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  static __device__ __forceinline__ R shfl_xor(R v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  static __device__ __forceinline__ bool positive(R v) {  // on the bits: no FP64 compare
+    const long long b = __double_as_longlong(v);
+    return b > 0ll && b < 0x7ff0000000000000ll;
+  }
+  static __device__ __forceinline__ R rsqrt(R v) { return ::rsqrt(v); }
+  static __device__ __forceinline__ R from_f(float x) { return (double)x; }
+  static __device__ __forceinline__ R from_f2(float hi, float lo) { return (double)hi + (double)lo; }
+  static __device__ __forceinline__ float to_f(R v) { return (float)v; }
+  static __device__ __forceinline__ R one() { return 1.0; }
+  static __device__ __forceinline__ R zero() { return 0.0; }
+  static __device__ __forceinline__ Lg log1p_(R v) { return ::log1p(v); }
+  static __device__ __forceinline__ Lg lshfl_xor(Lg v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+};
+
+template <>
+struct PairArith<ff> {
+  typedef ff R;
+  typedef float Lg;
+  static __device__ __forceinline__ R fma(R a, R b, R c) { return ff_fma(a, b, c); }
+  static __device__ __forceinline__ R mul(R a, R b) { return ff_mul(a, b); }
+  static __device__ __forceinline__ R add(R a, R b) { return ff_add(a, b); }
+  static __device__ __forceinline__ R neg(R a) { return ff_neg(a); }
+  static __device__ __forceinline__ R flip(R v, bool f) { return f ? ff_neg(v) : v; }
+  static __device__ __forceinline__ R shfl(R v, int src) {
+    return ff_make(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+  }
+  static __device__ __forceinline__ R shfl_xor(R v, int m) {
+    return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+  }
+  static __device__ __forceinline__ bool positive(R v) {
+    const unsigned b = __float_as_uint(v.hi);
+    return (b >> 31) == 0u && b != 0u && b < 0x7f800000u;
+  }
+  static __device__ __forceinline__ R rsqrt(R v) { return ff_rsqrt(v); }
+  static __device__ __forceinline__ R from_f(float x) { return ff_from(x); }
+  static __device__ __forceinline__ R from_f2(float hi, float lo) { return ff_make(hi, lo); }
+  static __device__ __forceinline__ float to_f(R v) { return v.hi; }  // hi is hi + lo rounded to float
+  static __device__ __forceinline__ R one() { return ff_from(1.f); }
+  static __device__ __forceinline__ R zero() { return ff_from(0.f); }
+  // log1p(hi + lo) = log1p(hi) + lo / (1 + hi) to first order; float accuracy
+  static __device__ __forceinline__ Lg log1p_(R v) { return log1pf(v.hi) + v.lo / (1.f + v.hi); }
+  static __device__ __forceinline__ Lg lshfl_xor(Lg v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+};
+
+// Per-user solve by eight lanes: lane (c, p) of the group works on the
 // real (p = 0) or imaginary (p = 1) part of every complex value it computes,
 // and the partner lane (lane ^ 4) supplies the other part by one exchange.
 // An FP64 warp instruction costs the same for any number of active lanes, so
@@ -387,33 +454,28 @@ static __device__ __noinline__ bool small_solve_dispatch(int Nr, int d, int c, b
 //   * U = UW (I + M)^{-1} is solved row-parallel (lane c, row c of UW, by
 //     v R^H = w then u R = v), so (I + M)^{-1} is never formed;
 //   * pivot tests compare bit patterns instead of issuing FP64 compares.
-// Same algebra as small_solve_grp.
-template <int NR, int DD>
-__device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const float2* Zrow0, int ldz, int own0,
-                                 float2* U, float2* UW, double* logdet, bool want_u, bool want_ld) {
-  typedef Cx<double> C;
-  const unsigned full = 0xffffffffu;
+// Same algebra as small_solve_grp; A = PairArith<double> or PairArith<ff>.
+template <class A, int NR, int DD>
+__device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const float2* Qlo, const float2* Zrow0,
+                                 int ldz, int own0, float2* U, float2* UW, double* logdet, bool want_u, bool want_ld) {
+  typedef typename A::R R;
+  typedef typename A::Lg Lg;
+  typedef Cx<R> C;
   const int lane = threadIdx.x & 31, gb = lane & ~7;
-  // s v with s = +1 on the imaginary lane and -1 on the real lane (sign bit flip)
-  const unsigned long long smask = p ? 0ull : 0x8000000000000000ull;
-  auto sg = [&](double v) { return __longlong_as_double(__double_as_longlong(v) ^ (long long)smask); };
+  // s v with s = +1 on the imaginary lane and -1 on the real lane
+  auto sg = [&](R v) { return A::flip(v, p == 0); };
   // own part of conj(v)
-  auto ownj = [&](C v) { return p ? __longlong_as_double(__double_as_longlong(v.y) ^ (long long)0x8000000000000000ull) : v.x; };
+  auto ownj = [&](C v) { return p ? A::flip(v.y, true) : v.x; };
   auto own = [&](C v) { return p ? v.y : v.x; };
   auto oth = [&](C v) { return p ? v.x : v.y; };
-  auto join = [&](double o) {
-    const double t = __shfl_xor_sync(full, o, 4);
-    return p ? mk<double>(t, o) : mk<double>(o, t);
+  auto join = [&](R o) {
+    const R t = A::shfl_xor(o, 4);
+    return p ? mk<R>(t, o) : mk<R>(o, t);
   };
   // the whole complex value v of the lanes of column col
   auto from_col = [&](C v, int col) {
     const int src = gb + 4 * p + col;
-    return mk<double>(__shfl_sync(full, v.x, src), __shfl_sync(full, v.y, src));
-  };
-  // a positive, finite pivot, tested on its bits (no FP64 compare)
-  auto positive = [](double v) {
-    const long long b = __double_as_longlong(v);
-    return b > 0ll && b < 0x7ff0000000000000ll;
+    return mk<R>(A::shfl(v.x, src), A::shfl(v.y, src));
   };
   // products by parts (a, b whole): own(a b) = a.x own(b) + s a.y oth(b),
   // own(conj(a) b) = a.x own(b) - s a.y oth(b), own(a conj(b)) = -s a.x own(b) + a.y oth(b)
@@ -421,30 +483,34 @@ __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const
 
   // Q = L L^H, row c of L by lane c; afterwards every lane holds all of L
   C L[NR][NR];
-  double inv[NR];
+  R inv[NR];
   {
-    double t0[NR];  // own part of Q[c][j] = conj(Q[j][c]), j <= c
+    R t0[NR];  // own part of Q[c][j] = conj(Q[j][c]), j <= c (high + low parts)
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      float2 v = make_float2(0.f, 0.f);
-      if (j <= c && c < NR) v = act ? Qp[j * NR - (j * (j - 1)) / 2 + (c - j)] : make_float2(j == c ? 1.f : 0.f, 0.f);
-      t0[j] = (double)(p ? -v.y : v.x);
+      float2 v = make_float2(0.f, 0.f), vl = make_float2(0.f, 0.f);
+      if (j <= c && c < NR) {
+        const int q = j * NR - (j * (j - 1)) / 2 + (c - j);
+        v = act ? Qp[q] : make_float2(j == c ? 1.f : 0.f, 0.f);
+        if (act) vl = Qlo[q];
+      }
+      t0[j] = A::from_f2(p ? -v.y : v.x, p ? -vl.y : vl.x);
     }
     C lrow[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      double t = t0[j];
+      R t = t0[j];
 #pragma unroll
       for (int k = 0; k < j; ++k)  // t -= own(L[c][k] conj(L[j][k]))
-        t = fma(-L[j][k].x, own(lrow[k]), fma(sg(L[j][k].y), oth(lrow[k]), t));
-      double dj = __shfl_sync(full, t, gb + j);  // the pivot, from the real lane of row j
-      if (!positive(dj)) {
+        t = A::fma(A::neg(L[j][k].x), own(lrow[k]), A::fma(sg(L[j][k].y), oth(lrow[k]), t));
+      R dj = A::shfl(t, gb + j);  // the pivot, from the real lane of row j
+      if (!A::positive(dj)) {
         ok = false;
-        dj = 1.0;
+        dj = A::one();
       }
-      const double rj = rsqrt(dj);
+      const R rj = A::rsqrt(dj);
       inv[j] = rj;
-      lrow[j] = join(t * rj);
+      lrow[j] = join(A::mul(t, rj));
 #pragma unroll
       for (int i = j + 1; i < NR; ++i) L[i][j] = from_col(lrow[j], i);
     }
@@ -455,104 +521,108 @@ __device__ bool small_solve_pair(int c, int p, bool act, const float2* Qp, const
 #pragma unroll
   for (int i = 0; i < NR; ++i) {
     const float2 zv = mine ? Zrow0[(long long)i * ldz + own0 + c] : make_float2(0.f, 0.f);
-    double t = (double)(p ? zv.y : zv.x);
+    R t = A::from_f(p ? zv.y : zv.x);
 #pragma unroll
-    for (int k = 0; k < i; ++k) t = fma(-L[i][k].x, own(x[k]), fma(-sg(L[i][k].y), oth(x[k]), t));
-    x[i] = join(t * inv[i]);
+    for (int k = 0; k < i; ++k)
+      t = A::fma(A::neg(L[i][k].x), own(x[k]), A::fma(A::neg(sg(L[i][k].y)), oth(x[k]), t));
+    x[i] = join(A::mul(t, inv[i]));
   }
   // column c of M = X^H X; row c of M is its conjugate (M Hermitian)
   C mcol[DD];
 #pragma unroll
   for (int a = 0; a < DD; ++a) {
-    double t = 0.0;
+    R t = A::zero();
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
       const C xa = from_col(x[i], a);
-      t = fma(xa.x, own(x[i]), fma(-sg(xa.y), oth(x[i]), t));
+      t = A::fma(xa.x, own(x[i]), A::fma(A::neg(sg(xa.y)), oth(x[i]), t));
     }
     mcol[a] = join(t);
   }
   // I + M = R R^H, row c of R by lane c (pivots kept minus one for log1p)
-  C R[DD][DD];
-  double rinv[DD];
-  double mypiv = 0.0;
+  C Rf[DD][DD];
+  R rinv[DD];
+  R mypiv = A::zero();
   {
     C rrow[DD];
 #pragma unroll
     for (int j = 0; j < DD; ++j) {
-      double t = ownj(mcol[j]);
+      R t = ownj(mcol[j]);
 #pragma unroll
-      for (int k = 0; k < j; ++k) t = fma(-R[j][k].x, own(rrow[k]), fma(sg(R[j][k].y), oth(rrow[k]), t));
-      double dm1 = __shfl_sync(full, t, gb + j);  // pivot - 1
-      double dj = 1.0 + dm1;
-      if (!positive(dj)) {
+      for (int k = 0; k < j; ++k) t = A::fma(A::neg(Rf[j][k].x), own(rrow[k]), A::fma(sg(Rf[j][k].y), oth(rrow[k]), t));
+      R dm1 = A::shfl(t, gb + j);  // pivot - 1
+      R dj = A::add(A::one(), dm1);
+      if (!A::positive(dj)) {
         ok = false;
-        dm1 = 0.0;
-        dj = 1.0;
+        dm1 = A::zero();
+        dj = A::one();
       }
       if (j == c) mypiv = dm1;
-      const double rj = rsqrt(dj);
+      const R rj = A::rsqrt(dj);
       rinv[j] = rj;
-      rrow[j] = join(t * rj);
+      rrow[j] = join(A::mul(t, rj));
 #pragma unroll
-      for (int i = j + 1; i < DD; ++i) R[i][j] = from_col(rrow[j], i);
+      for (int i = j + 1; i < DD; ++i) Rf[i][j] = from_col(rrow[j], i);
     }
   }
   // log det(I + M): lane c contributes log1p of pivot c, summed over the columns
-  double ld = (want_ld && c < DD) ? log1p(mypiv) : 0.0;
-  ld += __shfl_xor_sync(full, ld, 1);
-  ld += __shfl_xor_sync(full, ld, 2);
-  if (c == 0 && p == 0) *logdet = ld;
+  Lg ld = (want_ld && c < DD) ? A::log1p_(mypiv) : (Lg)0;
+  ld += A::lshfl_xor(ld, 1);
+  ld += A::lshfl_xor(ld, 2);
+  if (c == 0 && p == 0) *logdet = (double)ld;
   if (!want_u) return ok;
   // column c of UW = L^{-H} x
   C y[NR];
 #pragma unroll
   for (int i = NR - 1; i >= 0; --i) {
-    double t = own(x[i]);
+    R t = own(x[i]);
 #pragma unroll
-    for (int k = i + 1; k < NR; ++k) t = fma(-L[k][i].x, own(y[k]), fma(sg(L[k][i].y), oth(y[k]), t));
-    y[i] = join(t * inv[i]);
-    if (mine && ok) reinterpret_cast<float*>(UW + i * DD + c)[p] = (float)own(y[i]);
+    for (int k = i + 1; k < NR; ++k) t = A::fma(A::neg(L[k][i].x), own(y[k]), A::fma(sg(L[k][i].y), oth(y[k]), t));
+    y[i] = join(A::mul(t, inv[i]));
+    if (mine && ok) reinterpret_cast<float*>(UW + i * DD + c)[p] = A::to_f(own(y[i]));
   }
   // row c of UW (own parts), gathered from the column lanes
-  double w[DD];
+  R w[DD];
 #pragma unroll
-  for (int b = 0; b < DD; ++b) w[b] = 0.0;
+  for (int b = 0; b < DD; ++b) w[b] = A::zero();
 #pragma unroll
   for (int i = 0; i < NR; ++i)
 #pragma unroll
     for (int b = 0; b < DD; ++b) {
-      const double v = __shfl_sync(full, own(y[i]), gb + 4 * p + b);
+      const R v = A::shfl(own(y[i]), gb + 4 * p + b);
       if (i == c) w[b] = v;
     }
   // row c of U = UW (R R^H)^{-1}: v R^H = w, then u R = v
   C v[DD], u[DD];
 #pragma unroll
   for (int j = 0; j < DD; ++j) {
-    double t = w[j];
+    R t = w[j];
 #pragma unroll
     for (int k = 0; k < j; ++k)  // t -= own(v_k conj(R[j][k]))
-      t = fma(sg(v[k].x), own(R[j][k]), fma(-v[k].y, oth(R[j][k]), t));
-    v[j] = join(t * rinv[j]);
+      t = A::fma(sg(v[k].x), own(Rf[j][k]), A::fma(A::neg(v[k].y), oth(Rf[j][k]), t));
+    v[j] = join(A::mul(t, rinv[j]));
   }
 #pragma unroll
   for (int j = DD - 1; j >= 0; --j) {
-    double t = own(v[j]);
+    R t = own(v[j]);
 #pragma unroll
     for (int k = j + 1; k < DD; ++k)  // t -= own(u_k R[k][j])
-      t = fma(-u[k].x, own(R[k][j]), fma(-sg(u[k].y), oth(R[k][j]), t));
-    u[j] = join(t * rinv[j]);
-    if (act && ok && c < NR) reinterpret_cast<float*>(U + c * DD + j)[p] = (float)own(u[j]);
+      t = A::fma(A::neg(u[k].x), own(Rf[k][j]), A::fma(A::neg(sg(u[k].y)), oth(Rf[k][j]), t));
+    u[j] = join(A::mul(t, rinv[j]));
+    if (act && ok && c < NR) reinterpret_cast<float*>(U + c * DD + j)[p] = A::to_f(own(u[j]));
   }
   return ok;
 }
 
+template <class A>
 static __device__ __noinline__ bool small_solve_pair_dispatch(int Nr, int d, int c, int p, bool act,
-                                                              const float2* Qp, const float2* Zrow0, int ldz,
-                                                              int own0, float2* U, float2* UW, double* logdet,
-                                                              bool want_u, bool want_ld) {
+                                                              const float2* Qp, const float2* Qlo,
+                                                              const float2* Zrow0, int ldz, int own0, float2* U,
+                                                              float2* UW, double* logdet, bool want_u,
+                                                              bool want_ld) {
 #define AMM_SP(a, b) \
-  if (Nr == a && d == b) return small_solve_pair<a, b>(c, p, act, Qp, Zrow0, ldz, own0, U, UW, logdet, want_u, want_ld);
+  if (Nr == a && d == b) \
+    return small_solve_pair<A, a, b>(c, p, act, Qp, Qlo, Zrow0, ldz, own0, U, UW, logdet, want_u, want_ld);
   AMM_SP(1, 1)
   AMM_SP(2, 1) AMM_SP(2, 2)
   AMM_SP(3, 1) AMM_SP(3, 2) AMM_SP(3, 3)
@@ -873,9 +943,68 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
 // ------------------------------------------------------- per-user phases
 // S3a: upper triangle of Q_r = sigma^2 I + sum over streams other than the
 // user's own of z z^H (sigma^2 = 1 after normalisation).  zget(row, col).
+// Entries of z z^H summed over many streams can be far larger than the
+// noise term (about 1e6 against 1 for a cell-centre user of the seven-cell
+// layout), where FP32 rounding of the sum would blur the noise floor that
+// eq. (9) resolves; so each entry is a compensated dot product (the
+// products split exactly by FMA, the sums by two_sum, the rounding errors
+// accumulated separately: about twice FP32 precision), stored as a high
+// part (sQ, read by the FP32 solves) and a low part (sQ + CK np, read by
+// the FP64 and float-float solves).
+// One entry sum_c z_a(c) conj(z_b(c)) over columns [c0, c1) except
+// [skip0, skip1), as a compensated dot product (the products split exactly by
+// FMA, the sums by two_sum, the rounding errors accumulated apart): about
+// twice FP32 precision.  Four interleaved chains per part keep the FP32 pipe
+// busy; zget(row, col).  Returns (re, im) in float-float.
+template <class ZGet>
+__device__ __forceinline__ void cov_entry(ZGet zget, int ra, int rb, int c0, int c1, int skip0, int skip1, ff* re,
+                                          ff* im) {
+  float sr[4] = {0.f, 0.f, 0.f, 0.f}, cr[4] = {0.f, 0.f, 0.f, 0.f};
+  float si[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+  auto acc = [](float& sum, float& comp, float x, float y) {
+    const float pr = __fmul_rn(x, y);
+    const float pe = fmaf(x, y, -pr);  // x y = pr + pe exactly
+    const ff t = two_sum(sum, pr);
+    sum = t.hi;
+    comp = __fadd_rn(comp, __fadd_rn(t.lo, pe));
+  };
+  for (int c = c0; c < c1; c += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int cc = c + u;
+      float2 za = make_float2(0.f, 0.f), zb = make_float2(0.f, 0.f);
+      if (cc < c1 && (cc < skip0 || cc >= skip1)) {
+        za = zget(ra, cc);
+        zb = zget(rb, cc);
+      }
+      acc(sr[u], cr[u], za.x, zb.x);
+      acc(sr[u], cr[u], za.y, zb.y);
+      acc(si[u], ci[u], za.y, zb.x);
+      acc(si[u], ci[u], -za.x, zb.y);
+    }
+  }
+  ff R = fast_two_sum(sr[0], cr[0]), I = fast_two_sum(si[0], ci[0]);
+#pragma unroll
+  for (int u = 1; u < 4; ++u) {
+    R = ff_add(R, fast_two_sum(sr[u], cr[u]));
+    I = ff_add(I, fast_two_sum(si[u], ci[u]));
+  }
+  *re = R;
+  *im = I;
+}
+
+// S3a: upper triangle of Q_r = sigma^2 I + sum over streams other than the
+// user's own of z z^H (sigma^2 = 1 after normalisation).  zget(row, col).
+// Entries of z z^H summed over many streams can be far larger than the
+// noise term (about 1e6 against 1 for a cell-centre user of the seven-cell
+// layout), where FP32 rounding of the sum would blur the noise floor that
+// eq. (9) resolves; so each entry is a compensated dot product (cov_entry),
+// stored as a high part (sQ, read by the FP32 solves) and a low part
+// (sQ + CK np, read by the FP64 and float-float solves).
 template <class ZGet>
 __device__ __forceinline__ void covariance_phase(const InstDesc& D, const Layout& Ly, ZGet zget, float2* sQ) {
   const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn, np = Ly.np;
+  float2* sQlo = sQ + Ly.CK * np;
   for (int e = threadIdx.x; e < Ly.CK * np; e += blockDim.x) {
     const int r = e / np;
     int q = e - r * np, a = 0;
@@ -885,12 +1014,11 @@ __device__ __forceinline__ void covariance_phase(const InstDesc& D, const Layout
     }
     const int bb = a + q;
     const int own0 = (r / K) * n + (r % K) * d;
-    float2 acc = make_float2(a == bb ? 1.f : 0.f, 0.f);
-    for (int c = 0; c < Cn; ++c) {
-      if (c >= own0 && c < own0 + d) continue;
-      acc = cjfma(zget(r * Nr + bb, c), zget(r * Nr + a, c), acc);  // z_a conj(z_b)
-    }
-    sQ[e] = acc;
+    ff re, im;
+    cov_entry(zget, r * Nr + a, r * Nr + bb, 0, Cn, own0, own0 + d, &re, &im);
+    if (a == bb) re = ff_add(re, ff_from(1.f));
+    sQ[e] = make_float2(re.hi, im.hi);
+    sQlo[e] = make_float2(re.lo, im.lo);
   }
 }
 
@@ -898,31 +1026,34 @@ struct NoIdle {
   __device__ void operator()() const {}
 };
 
-// S3b/S4: the per-user solves (eight lanes per user in FP64, four in FP32),
-// then rho = sum alpha_r R_r (block-uniform; 0 when want_ld is false and the
-// rates are skipped).  The own-stream block of user r is rows r Nr.., columns
+// S3b/S4: the per-user solves (eight lanes per user in FP64 or float-float,
+// four in FP32), writing U, U W and the rates R_r (0 when want_ld is false
+// and the rates are skipped); rho_sum_ff / rho_sum_exact sum them.  The own-stream block of user r is rows r Nr.., columns
 // own0.. of Z (row stride ldz).  Zown: when non-null, the users' own-stream blocks in compact form (user r
 // at Zown + r Nr d, row stride d), read instead of Z.  idle(): run by the
 // warps that hold no user (all of their lanes), before the closing barrier;
 // it must not use block-wide barriers.
 template <class T, class Idle = NoIdle>
-__device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& Ly, const float2* Z, int ldz,
+__device__ __forceinline__ void solve_phase(const InstDesc& D, const Layout& Ly, const float2* Z, int ldz,
                                               const float2* sQ, float2* sU, float2* sUW, double* sRho,
                                               const float* alpha_u, bool want_u, bool want_ld, double* red,
-                                              int* fail, const float2* Zown = nullptr, Idle idle = Idle()) {
+                                              int* fail, const float2* Zown = nullptr, Idle idle = Idle(),
+                                              int r0 = 0, int nusers = -1) {
   const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, np = Ly.np, CK = Ly.CK;
+  const int NU = nusers < 0 ? CK : nusers;  // users r0 .. r0 + NU - 1 are solved
   // An FP64 warp instruction costs the same however few of its lanes are
   // active (on this part about 64 cycles for one warp, and one per 19 cycles
   // for the whole SM), so the users are packed densely: FP64 solves take
   // eight lanes per user (column x real/imaginary part, small_solve_pair),
   // FP32 solves four (column).  The trip count is warp-uniform (the solve
   // shuffles).
-  constexpr int kLanes = sizeof(T) == 8 ? 8 : 4;
+  constexpr bool kPair = !std::is_same<T, float>::value;  // FP64 or float-float: eight lanes per user
+  constexpr int kLanes = kPair ? 8 : 4;
   bool had_user = false;
-  for (int base = 0; base < kLanes * CK; base += blockDim.x) {
+  for (int base = 0; base < kLanes * NU; base += blockDim.x) {
     const int e = base + threadIdx.x;
-    const bool act = e < kLanes * CK;
-    const int r = act ? e / kLanes : 0, c = e & 3, ri = (e / 4) & (kLanes / 4 - 1);
+    const bool act = e < kLanes * NU;
+    const int r = r0 + (act ? e / kLanes : 0), c = e & 3, ri = (e / 4) & (kLanes / 4 - 1);
     if (!__any_sync(0xffffffffu, act)) continue;  // warps without a user skip the solve
     had_user = true;
     const int own0 = Zown ? 0 : (r / K) * n + (r % K) * d;
@@ -930,9 +1061,9 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
     const int ldr = Zown ? d : ldz;
     double ld = 0.0;
     bool ok;
-    if (kLanes == 8)
-      ok = small_solve_pair_dispatch(Nr, d, c, ri, act, sQ + r * np, zr, ldr, own0, sU + r * Nr * d,
-                                     sUW + r * Nr * d, &ld, want_u, want_ld);
+    if constexpr (kPair)
+      ok = small_solve_pair_dispatch<PairArith<T>>(Nr, d, c, ri, act, sQ + r * np, sQ + (CK + r) * np, zr, ldr,
+                                                   own0, sU + r * Nr * d, sUW + r * Nr * d, &ld, want_u, want_ld);
     else
       ok = small_solve_dispatch<T>(Nr, d, c, act, sQ + r * np, zr, ldr, own0, sU + r * Nr * d, sUW + r * Nr * d,
                                    &ld, want_u, want_ld);
@@ -943,6 +1074,21 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
   }
   if (!had_user) idle();
   __syncthreads();
+}
+
+// rho = sum alpha_r R_r over the users (block-uniform).  In the iterations
+// it only feeds the stage and stopping tests and the state returned by
+// amm_get_state, so it is summed in float-float (about 1e-14 relative here,
+// far below the FP32 rounding of the Z it comes from) without FP64
+// instructions; the final WSR evaluation sums it in FP64.  The float-float
+// scratch sits past the FP64 scratch of block_sum in `red`.  Both contain
+// __syncthreads().
+__device__ __forceinline__ ff rho_sum_ff(const double* sRho, const float* alpha_u, int CK, double* red) {
+  ff part = ff_from(0.f);
+  for (int r = threadIdx.x; r < CK; r += blockDim.x) part = ff_add(part, ff_mul(ff_from_double(sRho[r]), ff_from(alpha_u[r])));
+  return block_sum_ff(part, reinterpret_cast<float*>(red) + 80);
+}
+__device__ __forceinline__ double rho_sum_exact(const double* sRho, const float* alpha_u, int CK, double* red) {
   double part = 0.0;
   for (int r = threadIdx.x; r < CK; r += blockDim.x) part += (double)alpha_u[r] * sRho[r];
   return block_sum(part, red);
@@ -955,11 +1101,13 @@ __device__ __forceinline__ double solve_phase(const InstDesc& D, const Layout& L
 template <class ZGet, class Sink>
 __device__ __forceinline__ void gradient_rhs_phase(const InstDesc& D, const Layout& Ly, ZGet zhat,
                                                    const float2* sU, const float2* sP, const float* alpha_u,
-                                                   Sink sink) {
-  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn, CK = Ly.CK;
+                                                   Sink sink, int cbeg = 0, int cend = -1) {
+  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, CK = Ly.CK;
+  const int Cn = cend < 0 ? Ly.Cn : cend;  // columns cbeg .. Cn - 1 (global numbering)
+  const int ncol = Cn - cbeg;
   int tpu = (int)blockDim.x / CK;
   if (tpu < 1) tpu = 1;
-  if (tpu > Cn) tpu = Cn;
+  if (tpu > ncol) tpu = ncol;
   const int upp = (int)blockDim.x / tpu;  // users per pass
   const int rr = (int)threadIdx.x / tpu, c0 = (int)threadIdx.x - rr * tpu;
   for (int r = rr; rr < upp && r < CK; r += upp) {
@@ -974,7 +1122,7 @@ __device__ __forceinline__ void gradient_rhs_phase(const InstDesc& D, const Layo
           Pr[a][s] = sP[(r * Nr + a) * d + s];
         }
     const float sc2 = 2.f * alpha_u[r];
-    for (int c = c0; c < Cn; c += tpu) {
+    for (int c = cbeg + c0; c < Cn; c += tpu) {
       float2 zh[kMaxNr];
 #pragma unroll
       for (int a = 0; a < kMaxNr; ++a)
@@ -1017,19 +1165,20 @@ __device__ __forceinline__ bool need_rate(int stage, int mode, int it, int n_ite
   return stage != 2 || mode != kFixed || it + 1 == n_iters;
 }
 
-__device__ __forceinline__ void stage_logic(int* ctrl, double rho, double rho_prev, int mode, double eps1,
-                                            double eps2, int switch_iter, int step_rule, int tc) {
-  // |R^t - R^{t-1}| / R^{t-1} <= eps, tested as |R^t - R^{t-1}| <= eps |R^{t-1}|
-  // (no FP64 division on the single thread that runs this)
+__device__ __forceinline__ void stage_logic(int* ctrl, ff rho, ff rho_prev, int mode, float eps1, float eps2,
+                                            int switch_iter, int step_rule, int tc) {
+  // |R^t - R^{t-1}| / R^{t-1} <= eps, tested as |R^t - R^{t-1}| <= eps |R^{t-1}| with the
+  // difference in float-float and the comparison in FP32 (a decision can differ
+  // from an exact one only within about 1e-7 of the threshold)
   const int t = ctrl[0];
-  const bool have_prev = !isnan(rho_prev);
-  const double diff = fabs(rho - rho_prev), ref = fabs(rho_prev);
+  const bool have_prev = !isnan(rho_prev.hi);
+  const float diff = fabsf(ff_add(rho, ff_neg(rho_prev)).hi), ref = fabsf(rho_prev.hi);
   int stop = 0;
-  if (mode == kTolerance && ctrl[3] == 2 && have_prev && ref > 0.0 && diff <= eps2 * ref) stop = 1;
+  if (mode == kTolerance && ctrl[3] == 2 && have_prev && ref > 0.f && diff <= eps2 * ref) stop = 1;
   int stage = ctrl[1], si = ctrl[2];
   if (!stop) {
     if (stage == 1) {
-      const bool go = (switch_iter >= 1) ? (t >= switch_iter) : (have_prev && ref > 0.0 && diff <= eps1 * ref);
+      const bool go = (switch_iter >= 1) ? (t >= switch_iter) : (have_prev && ref > 0.f && diff <= eps1 * ref);
       if (go) {
         stage = 2;
         si = 0;

@@ -119,7 +119,7 @@ __host__ __device__ inline Layout plan_layout(const InstDesc& D, int budget, int
   L.off_cell = off; off += 4 * kMaxCells * 8;
   L.off_U = off;    off += L.CK * D.Nr * D.d * 8;
   L.off_UW = off;   off += L.CK * D.Nr * D.d * 8;
-  L.off_Q = off;    off += L.CK * L.np * 8;
+  L.off_Q = off;    off += 2 * L.CK * L.np * 8;  // high parts, then low parts
   L.off_rho = off;  off += L.CK * 8;
   L.off_y = off;    off += L.m * 8;
   L.off_z = off;    off += L.m * 8;

@@ -31,7 +31,7 @@ __global__ void normalize_kernel(const InstDesc* desc, const float2* Hin, const 
 __global__ void init_kernel(const InstDesc* desc, const float2* V0, const float* P, float2* V, float2* Vprev,
                             Scalars* sc, float* gamma_c, int switch_iter);
 cudaError_t iterate_set_smem(int bytes);
-void iterate_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p);
+void iterate_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p);
 amm_status check_opts(const amm_opts& o, const char** why);
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
@@ -207,12 +207,12 @@ extern "C" amm_status amm_solve_noalloc(int batch, const amm_dims* dims, const a
   if (n_iters > 0) {
     p.n_iters = n_iters;
     p.mode = kFixed;
-    iterate_launch(o.fp64_solves != 0, batch, Ly.total, st, p);
+    iterate_launch(o.fp64_solves, batch, Ly.total, st, p);
   }
   p.n_iters = 1;
   p.mode = kEvalWsr;
   p.wsr_out = wsr_out;
-  iterate_launch(true, batch, Ly.total, st, p);
+  iterate_launch(1, batch, Ly.total, st, p);
   if ((e = cudaGetLastError())) return noalloc_fail(err, err_len, AMM_ECUDA, cudaGetErrorString(e));
   return AMM_OK;
 }

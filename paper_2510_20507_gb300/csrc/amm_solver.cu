@@ -18,7 +18,7 @@
 //   S6  Y_r = 2 alpha_r U_r W_r (U_r^H Zhat_r - S_r), S_r selecting the user's own
 //       d x d identity block; then G_j = Htilde_j^H Y[:, cols of j] equals the
 //       gradient (14) at Vhat exactly, without forming F_k.
-//   S7  Vtilde = Vhat - gamma G, ||Vtilde_k||_F^2 (FP64 accumulation), projection (15).
+//   S7  Vtilde = Vhat - gamma G, ||Vtilde_k||_F^2 (float-float accumulation), projection (15).
 #include <math.h>
 #include <stdio.h>
 
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   __shared__ int s_fail;
   __shared__ int s_ctrl[8];
   __shared__ float s_bcast;
-  __shared__ double s_rhoprev;
+  __shared__ ff s_rhoprev;  // R^{t-1} in float-float (hi NaN: none yet)
 
   const int b = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const InstDesc D = p.desc[b];
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     cellf[32 + k] = p.P[D.c_off + k];
     cellf[48 + k] = gamma_cg[k];
   }
-  if (tid == 0) s_rhoprev = scg->rho_prev;
+  if (tid == 0) s_rhoprev = ff_from_double(scg->rho_prev);
   const float* Pc = cellf + 32;
   float* gamma_c = cellf + 48;
   float2* Vg = p.V + D.v_off;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   __syncthreads();
 
   const int n_iters = (p.mode == kEvalWsr) ? 1 : p.n_iters;
-  double rho = 0.0;
+  ff rho = ff_from(0.f);
   for (int it = 0; it < n_iters; ++it) {
     const int t = s_ctrl[0];
     const float omega = (p.extrapolate && t >= 3) ? (float)(t - 2) / (float)(t + 1) : 0.f;
@@ -178,16 +178,18 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     covariance_phase(D, Ly, [&](int row, int c) { return Zc[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
     // ---- S3b/S4: FP64 small solves, one thread per user; rho = WSR(V^{t-1})
-    rho = solve_phase<T>(D, Ly, Zc, ldz, sQ, sU, sUW, sRho, alpha_u, p.mode != kEvalWsr,
-                         need_rate(s_ctrl[1], p.mode, it, n_iters), red, &s_fail);
+    const bool want_rate = need_rate(s_ctrl[1], p.mode, it, n_iters);
+    solve_phase<T>(D, Ly, Zc, ldz, sQ, sU, sUW, sRho, alpha_u, p.mode != kEvalWsr, want_rate, red, &s_fail);
     if (s_fail != kOk) break;
     if (p.mode == kEvalWsr) {
-      if (tid == 0) p.wsr_out[b] = rho / 0.69314718055994530942;
+      const double w = rho_sum_exact(sRho, alpha_u, Ly.CK, red);
+      if (tid == 0) p.wsr_out[b] = w / 0.69314718055994530942;
       break;
     }
+    rho = want_rate ? rho_sum_ff(sRho, alpha_u, Ly.CK, red) : ff_from(0.f);
     // ---- stage test of Algorithm 3 and the stopping test (thread 0)
     if (tid == 0)
-      stage_logic(s_ctrl, rho, s_rhoprev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
+      stage_logic(s_ctrl, rho, s_rhoprev, p.mode, (float)p.eps1, (float)p.eps2, p.switch_iter, p.step_rule, p.tc);
     __syncthreads();
     if (s_ctrl[4]) break;
     const int stage = s_ctrl[1];
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
       }
       const float2* Vc = vw.V[cur] + (long long)j * Nt * ldv;
       float2* Vn = vw.V[cur ^ 1] + (long long)j * Nt * ldv;
-      float nrm = 0.f;
+      ff nrm = ff_from(0.f);
       block_cgemm_tiled<1>(tile_g, Nt, n, m, Hj, ldh, Zp + j * n, ldz,
                            [&](int r, int c, float2 g) {
                              const long long idx = (long long)r * ldv + c;
@@ -234,10 +236,11 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
                              if (omega != 0.f) vh = csub(cscale(vh, 1.f + omega), cscale(Vn[idx], omega));
                              const float2 vt = csub(vh, cscale(g, gj));
                              Vn[idx] = vt;
-                             nrm += cabs2(vt);
+                             nrm = ff_add(nrm, ff_from(cabs2(vt)));
                            });
-      const double s = block_sum((double)nrm, red);  // block-uniform; all of Vtilde_j written
-      const float sj = (s > (double)Pc[j]) ? (float)sqrt((double)Pc[j] / s) : 1.f;
+      // ||Vtilde_j||^2 in float-float (block-uniform; all of Vtilde_j written), then eq. (15)
+      const ff s = block_sum_ff(nrm, reinterpret_cast<float*>(red) + 80);
+      const float sj = (s.hi > Pc[j]) ? sqrtf(Pc[j] / s.hi) : 1.f;
       if (sj != 1.f) {
         for (int e = tid; e < Nt * n; e += blockDim.x) {
           const int r = e / n, c = e - r * n;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   }
   if (tid == 0) {
     scg->t = s_ctrl[0];
-    scg->rho_prev = s_rhoprev;
+    scg->rho_prev = ff_to_double(s_rhoprev);
     for (int k = 0; k < C; ++k) gamma_cg[k] = gamma_c[k];
     scg->stage = s_ctrl[1];
     scg->stage_iter = s_ctrl[2];
@@ -305,11 +308,15 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
 // Host-side launchers (the capi translation unit does not see the templates).
 cudaError_t iterate_set_smem(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(iterate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(iterate_kernel<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(iterate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
-void iterate_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p) {
-  if (fp64) iterate_kernel<double><<<grid, kThreads, smem, st>>>(p);
+// solves: 0 FP32, 1 FP64, 2 float-float
+void iterate_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p) {
+  if (solves == 1) iterate_kernel<double><<<grid, kThreads, smem, st>>>(p);
+  else if (solves == 2) iterate_kernel<ff><<<grid, kThreads, smem, st>>>(p);
   else iterate_kernel<float><<<grid, kThreads, smem, st>>>(p);
 }
 

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   __shared__ int s_fail;
   __shared__ int s_ctrl[8];
   __shared__ float s_bcast;
-  __shared__ double s_rhoprev;
+  __shared__ ff s_rhoprev;  // R^{t-1} in float-float (hi NaN: none yet)
 
   const int b = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const InstDesc D = p.desc[b];
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   for (int r = tid; r < Ly.CK; r += blockDim.x) s_alpha[r] = p.alpha[D.u_off + r];
   if (tid == 0) {
     cellf[48] = gamma_cg[0];
-    s_rhoprev = scg->rho_prev;
+    s_rhoprev = ff_from_double(scg->rho_prev);
   }
   const float Pc = p.P[D.c_off];
   float* gamma_c = cellf + 48;
@@ -324,9 +324,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
 
   // the extrapolation can run beside the solves when the users fill warps 0-3
   // only (eight lanes per user in FP64, four in FP32) and the compact copy fits
-  constexpr int kSolveLanes = sizeof(SolveT) == 8 ? 8 : 4;
+  constexpr int kSolveLanes = std::is_same<SolveT, float>::value ? 4 : 8;
   const bool xo_ok = sZo != nullptr && kSolveLanes * Ly.CK <= 128 && blockDim.x == 256;
-  double rho = 0.0;
+  ff rho = ff_from(0.f);
   for (int it = 0; it < p.n_iters && s_fail == kOk; ++it) {
     const int t = s_ctrl[0];
     const float omega = (p.extrapolate && t >= 3) ? (float)(t - 2) / (float)(t + 1) : 0.f;
@@ -364,8 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       tc::fence_after_sync();
       for (int cc = 0; cc < nchunks; ++cc) {
         float v[16], vp[16];
-        tc::tmem_ld16(lane_addr + colD1[zc] + cc * 16, v);
-        tc::tmem_ld16(lane_addr + colD1[zc ^ 1] + cc * 16, vp);
+        tc::tmem_ld16x2(lane_addr + colD1[zc] + cc * 16, lane_addr + colD1[zc ^ 1] + cc * 16, v, vp);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = cc * 16 + j;
@@ -376,15 +375,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       }
       tc::fence_before_sync();
     };
+    const bool want_rate = need_rate(s_ctrl[1], p.mode, it, p.n_iters);
     if (overlap)
-      rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true,
-                                need_rate(s_ctrl[1], p.mode, it, p.n_iters), red, &s_fail, sZo, extrap_idle);
+      solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true, want_rate, red, &s_fail, sZo,
+                          extrap_idle);
     else
-      rho = solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true,
-                                need_rate(s_ctrl[1], p.mode, it, p.n_iters), red, &s_fail);
+      solve_phase<SolveT>(D, Ly, Zs, ldz, sQ, sU, sUW, sRho, alpha_u, true, want_rate, red, &s_fail);
     if (s_fail != kOk) break;
+    rho = want_rate ? rho_sum_ff(sRho, alpha_u, Ly.CK, red) : ff_from(0.f);
     if (tid == 0)
-      stage_logic(s_ctrl, rho, s_rhoprev, p.mode, p.eps1, p.eps2, p.switch_iter, p.step_rule, p.tc);
+      stage_logic(s_ctrl, rho, s_rhoprev, p.mode, (float)p.eps1, (float)p.eps2, p.switch_iter, p.step_rule, p.tc);
     __syncthreads();
     if (s_ctrl[4]) break;
     const int stage = s_ctrl[1];
@@ -394,8 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       tc::fence_after_sync();
       for (int cc = half; cc < nchunks; cc += 2) {
         float v[16], vp[16];
-        tc::tmem_ld16(lane_addr + colD1[zc] + cc * 16, v);
-        tc::tmem_ld16(lane_addr + colD1[zc ^ 1] + cc * 16, vp);
+        tc::tmem_ld16x2(lane_addr + colD1[zc] + cc * 16, lane_addr + colD1[zc ^ 1] + cc * 16, v, vp);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = cc * 16 + j;
@@ -482,28 +481,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     // ---- S6/S7: G = H^H Y on the tensor cores
     if (!gemm(colD2, T.mn ? A1 : A2, T.K2p, T.mn, false)) break;
     const float gj = cellf[0];
-    float nrm = 0.f;
+    ff nrm = ff_from(0.f);
     // Vtilde = Vhat - gamma G into the V^{t-2} slot and the block's ||Vtilde||^2
     for (int cc = half; cc < nchunks; cc += 2) {
       float g[16], v[16], vp[16];
-      tc::tmem_ld16(lane_addr + colD2 + cc * 16, g);
-      tc::tmem_ld16(lane_addr + colV[cur] + cc * 16, v);
-      tc::tmem_ld16(lane_addr + colV[cur ^ 1] + cc * 16, vp);
+      tc::tmem_ld16x3(lane_addr + colD2 + cc * 16, lane_addr + colV[cur] + cc * 16,
+                      lane_addr + colV[cur ^ 1] + cc * 16, g, v, vp);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int c = cc * 16 + j;
         const float vh = (omega != 0.f) ? (1.f + omega) * v[j] - omega * vp[j] : v[j];
         float vt = vh - gj * g[j];
         if (!(c < n && R < 2 * Nt)) vt = 0.f;
-        nrm = fmaf(vt, vt, nrm);
+        nrm = ff_add(nrm, ff_from(vt * vt));
         v[j] = vt;
       }
       tc::tmem_st16(lane_addr + colV[cur ^ 1] + cc * 16, v);
     }
     tc::tmem_wait_st();
-    const double s = block_sum((double)nrm, red);
-    // projection (eq. (15)), then B1 = split(V^t) for the next forward GEMM
-    const float scale = (s > (double)Pc) ? (float)sqrt((double)Pc / s) : 1.f;
+    // ||Vtilde||^2 in float-float, then the projection (eq. (15)) and
+    // B1 = split(V^t) for the next forward GEMM
+    const ff s = block_sum_ff(nrm, reinterpret_cast<float*>(red) + 80);
+    const float scale = (s.hi > Pc) ? sqrtf(Pc / s.hi) : 1.f;
     for (int cc = half; cc < nchunks; cc += 2) {
       float v[16];
       tc::tmem_ld16(lane_addr + colV[cur ^ 1] + cc * 16, v);
@@ -533,8 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   if (s_fail == kOk || s_fail == kNotConv) {
     for (int cc = half; cc < nchunks; cc += 2) {
       float v[16], vp[16];
-      tc::tmem_ld16(lane_addr + colV[cur] + cc * 16, v);
-      tc::tmem_ld16(lane_addr + colV[cur ^ 1] + cc * 16, vp);
+      tc::tmem_ld16x2(lane_addr + colV[cur] + cc * 16, lane_addr + colV[cur ^ 1] + cc * 16, v, vp);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int c = cc * 16 + j;
@@ -553,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
   if (warp == 0) tc::tmem_dealloc(tbase, (unsigned)T.ncols);
   if (tid == 0) {
     scg->t = s_ctrl[0];
-    scg->rho_prev = s_rhoprev;
+    scg->rho_prev = ff_to_double(s_rhoprev);
     for (int k = 0; k < 1; ++k) gamma_cg[k] = gamma_c[k];
     scg->stage = s_ctrl[1];
     scg->stage_iter = s_ctrl[2];
@@ -571,11 +569,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
 
 cudaError_t tc_set_smem(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(tc_iterate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_iterate_kernel<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(tc_iterate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
-void tc_launch(bool fp64, int grid, int smem, cudaStream_t st, const IterParams& p, int prec) {
-  if (fp64) tc_iterate_kernel<double><<<grid, kThreads, smem, st>>>(p, prec);
+// solves: 0 FP32, 1 FP64, 2 float-float
+void tc_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p, int prec) {
+  if (solves == 1) tc_iterate_kernel<double><<<grid, kThreads, smem, st>>>(p, prec);
+  else if (solves == 2) tc_iterate_kernel<ff><<<grid, kThreads, smem, st>>>(p, prec);
   else tc_iterate_kernel<float><<<grid, kThreads, smem, st>>>(p, prec);
 }
 

@@ -166,8 +166,9 @@ __global__ void __launch_bounds__(kThreads) wmmse_kernel(IterParams p, float bis
     __syncthreads();
     covariance_phase(D, Ly, [&](int row, int c) { return sZ[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
-    const double rho = solve_phase<double>(D, Ly, sZ, ldz, sQ, sU, sUW, sRho, alpha_u, true, true, red, &s_fail);
+    solve_phase<double>(D, Ly, sZ, ldz, sQ, sU, sUW, sRho, alpha_u, true, true, red, &s_fail);
     if (s_fail != kOk) break;
+    const double rho = rho_sum_exact(sRho, alpha_u, Ly.CK, red);
     // V update per cell, eq. (12)
     for (int k = 0; k < C; ++k) {
       const float2* Hk = Hs + (long long)k * m * ldh;

@@ -69,3 +69,28 @@ def test_injected_allocation_failure_cleans_up(nth):
     g.step(5)
     assert np.all(np.isfinite(g.wsr())) and np.all(g.status() == 0)
     g.close()
+
+
+def test_cluster_wait_budget_exhausted_reports_timeout():
+    """The seven-cell cluster kernel with a one-cycle wait budget: the bulk
+    copies and the cluster exchange rounds run out, every instance reports
+    AMM_ETIMEOUT with WSR NaN, the launch returns, and a fresh context on
+    the same layout solves."""
+    import __graft_entry__ as ge
+    ge.build()
+    from gpu_util import round_inputs
+    insts = round_inputs(wl.hex7(n=256, count=8))
+    g = GpuRun(insts, spin_budget=1)
+    assert g.s.path == "cluster"
+    g.warmstart()
+    g.step(3)
+    st = g.status()
+    w = g.wsr()
+    g.close()
+    assert np.all(st == AMM_ETIMEOUT), st
+    assert np.all(np.isnan(w))
+    ok = GpuRun(insts[:2])
+    ok.warmstart()
+    ok.step(4)
+    assert np.all(ok.status() == 0) and np.all(np.isfinite(ok.wsr()))
+    ok.close()

@@ -3,7 +3,8 @@
 The target is a final WSR within 1e-3 relative of the oracle.  This solves
 the whole single-cell P sweep (7 x 1024 instances, Nt=64, K=16, Nr=4, d=4,
 50 iterations) on the GPU in the launch configuration bench.py times, for
-the plain FP32 path and the BF16X6 tensor-core path, and re-solves all 7168
+the plain FP32 path and the BF16X6 tensor-core path (with FP64 and with
+float-float per-user solves), and re-solves all 7168
 instances with the oracle on a spawn-started process pool over the host
 cores (about two minutes on 16 cores).
 
@@ -52,14 +53,14 @@ def oracle_refs():
     return [r for part in res for r in part]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
-def test_every_instance_within_gap(prec, oracle_refs):
+@pytest.mark.parametrize("prec,solves", [("fp32", 1), ("bf16x6", 1), ("bf16x6", 2)])
+def test_every_instance_within_gap(prec, solves, oracle_refs):
     import __graft_entry__ as ge
     ge.build()
     import workloads as wl
     from gpu_util import GpuRun, spawn_pool
     from oracle import parity as op
-    g = GpuRun(wl.single_cell_64(), precision=prec)
+    g = GpuRun(wl.single_cell_64(), precision=prec, fp64_solves=solves)
     g.warmstart()
     g.step(ITERS)
     got = g.wsr()

@@ -70,16 +70,35 @@ def test_perturbed_solve_without_perturbation_is_the_oracle():
 
 
 def test_each_perturbation_acts_and_spread_is_their_maximum():
-    """Every perturbation changes the result (it is applied), by FP32-sized
+    """Every perturbation changes the result (it is applied), by small
     amounts on this well-conditioned 10 dB instance; the spread is the
-    largest of those changes."""
+    largest of those changes; the noise runs differ by seed; an early stop
+    returns a value that reaches the requested level."""
     inst = wl.tiny_fp64(1)[0]
     ref = _solve_bits(inst, 12)
     w = sens.fp32_wsr_samples(inst, 12)
     rel = [abs(x - ref) / ref for x in w]
+    assert len(w) == len(sens.VARIANTS) == 12
     assert all(0 < r < 1e-5 for r in rel), rel
+    assert len(set(w[:sens.N_NOISE])) == sens.N_NOISE
     assert sens.fp32_spread(inst, 12) == max(rel)
     assert sens.fp32_spread(inst, 12, reference=ref) == max(rel)
+    early = sens.fp32_spread(inst, 12, reference=ref, stop_at=rel[0] / 2)
+    assert early == rel[0]
+
+
+def test_noise_perturbation_has_the_stated_size():
+    """One iteration with the per-step noise: the iterate moves by
+    STEP_NOISE relative (Frobenius, to within sampling error)."""
+    inst = wl.tiny_fp64(1)[0]
+    V0 = s.initial_precoder(inst.G0, inst.P)
+    st = s.AState(V=V0.copy(), Vprev=V0.copy())
+    s.ammmse_iteration(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, st, s.Options())
+    rng = np.random.default_rng(1)
+    xi = (rng.standard_normal(st.V.shape) + 1j * rng.standard_normal(st.V.shape)) / np.sqrt(2.0)
+    Vn = st.V * (1.0 + sens.STEP_NOISE * xi)
+    relchg = np.linalg.norm(Vn - st.V) / np.linalg.norm(st.V)
+    assert 0.5 * sens.STEP_NOISE < relchg < 2.0 * sens.STEP_NOISE
 
 
 def test_covariance_rounding_hook_rounds_to_complex64():

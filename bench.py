@@ -547,11 +547,28 @@ def run_gpu(args):
     return 0
 
 
+def _unrolled_worker(args):
+    """Oracle forward of the unrolled map (oracle.solvers.ammmse_unrolled) on
+    one instance of the unrolled workload: (index, WSR(V^T) in bits)."""
+    b, n, T, sw, gam = args
+    import numpy as np
+    import workloads as wl
+    from oracle import solvers as osv
+    inst = _round32(wl.unrolled_64(n=n, first=b, count=1)[0])
+    V0 = osv.initial_precoder(inst.G0, inst.P)
+    g = float(np.float32(gam))
+    return b, osv.ammmse_unrolled(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0, [g] * T,
+                                  switch_iter=sw)[1]
+
+
 def run_unrolled(args):
     """The differentiable unrolled workload: 1024 instances of Nt=64, K=16,
     Nr=2, d=2 at 20 dB, T=20 iterations, checkpoints every 5, forward
     (WSR) plus the hand-written adjoint (gradients in every gamma_t and in
     H) per step.  Metric: instance-gradients/s (one JSON line)."""
+    pool, cores = None, os.cpu_count() or 1
+    if not args.no_cpu_baseline:
+        pool = make_pool(cores)  # spawned before the first CUDA call
     import numpy as np
     import torch
     import workloads as wl
@@ -602,13 +619,33 @@ def run_unrolled(args):
             "traffic": None, "kernel": "u_forward_kernel + u_backward_kernel",
             "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                          f"(derived; {src} clocks)"}
+    # the CPU baseline: the oracle's forward of the unrolled map on a sample
+    # (the oracle has no adjoint; the gradients are checked in the tests
+    # against FP64 finite differences and a float64 autograd restatement),
+    # timed, and the reference of the forward WSR gap
+    cpu, parity = None, None
+    if pool is not None:
+        with torch.no_grad():
+            got = unrolled_wsr(solver, H.detach(), gam.detach(), al, s2, P, V0).cpu().numpy()
+        idx = list(range(0, n, max(1, n // 64)))[:64]
+        t0 = time.perf_counter()
+        res = pool.map(_unrolled_worker, [(b, n, T, sw, 0.004) for b in idx], chunksize=1)
+        dt = time.perf_counter() - t0
+        pool.close()
+        gaps = np.array([(got[b] - w) / w for b, w in res])
+        cpu = {"value": len(res) / dt, "unit": "instance-forwards/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(res)} instances (every {max(1, n // 64)}-th), forward WSR of the unrolled map only "
+                         f"(the oracle has no adjoint), numpy float64, one process per core, {dt:.1f} s"}
+        parity = {"forward_wsr_checked": len(res), "max_abs_gap": float(np.abs(gaps).max()),
+                  "median_abs_gap": float(np.median(np.abs(gaps))), "mean_signed_gap": float(gaps.mean()),
+                  "within_1e-3": int(np.sum(np.abs(gaps) <= 1e-3))}
     print(json.dumps({"metric": "instance-gradients/s (unrolled A-MMMSE, forward + adjoint)",
                       "value": n * args.steps / (ms / 1000.0), "unit": "instance-gradients/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "unrolled: Nt=64, K=16, Nr=2, d=2, P=20 dB, T=20, checkpoints every 5, "
                                              "stage II from iteration 4", "instances": n},
-                      "roofline": roof, "clocks": clk}))
+                      "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "parity": parity}))
     solver.close()
     return 0
 

@@ -109,8 +109,9 @@ typedef struct {
                            0: FP32.  The WSR evaluation of amm_wsr is FP64
                            whatever this says.  Other values: AMM_EINVAL. */
   int gemm_tile;        /* register tile of the FP32-path block GEMMs: 0 automatic
-                           (by instance size), 1: 4x4, 2: 2x2, 3: 4x2 (set by
-                           the autotuner); 0 */
+                           (per GEMM shape, the tile whose slowest thread does
+                           the least work), 1: 4x4, 2: 2x2, 3: 4x2, 4: 4x3,
+                           5: 2x5 (set by the autotuner); 0 */
   int cluster_cells;    /* multi-cell instances (2 <= cells <= 8) whose channel does
                            not fit one block's shared memory, on the FP32 GEMM path:
                            1 = one thread-block cluster per instance, one block per

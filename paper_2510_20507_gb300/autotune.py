@@ -7,7 +7,8 @@ a JSON file keyed by GPU, shape and class.  Accuracy classes and their
 candidates:
 
   "fp32"    FP32-level GEMMs: the FP32 FFMA path with each register tile of
-            its block GEMMs (gemm_tile 1: 4x4, 2: 2x2, 3: 4x2), and the
+            its block GEMMs (gemm_tile 1: 4x4, 2: 2x2, 3: 4x2, 4: 4x3,
+            5: 2x5; 0: the library's own pick by shape), and the
             tensor-core path with the six-product bf16 split (BF16X6), which
             computes the same GEMMs to FP32 accuracy;
   "bf16x3"  the tensor-core path with the three-product split;
@@ -27,8 +28,8 @@ import numpy as np
 from .amm import Opts, Solver, default_opts
 
 CLASSES = {
-    "fp32": [dict(precision="fp32", gemm_tile=1), dict(precision="fp32", gemm_tile=2),
-             dict(precision="fp32", gemm_tile=3), dict(precision="bf16x6", gemm_tile=0)],
+    "fp32": [dict(precision="fp32", gemm_tile=t) for t in (0, 1, 2, 3, 4, 5)] +
+            [dict(precision="bf16x6", gemm_tile=0)],
     "bf16x3": [dict(precision="bf16x3", gemm_tile=0)],
     "bf16": [dict(precision="bf16", gemm_tile=0)],
 }

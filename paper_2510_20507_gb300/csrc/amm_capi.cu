@@ -195,7 +195,7 @@ amm_status check_opts(const amm_opts& o, const char** why) {
   if ((o.step_rule == 2 || (o.step_rule == 0 && o.tc == 0)) && !(o.gamma_c > 0))
     return *why = "a fixed step needs gamma_c > 0", AMM_EINVAL;
   if (o.lanczos_steps < 1 || o.lanczos_steps > kMaxLanczos) return *why = "lanczos_steps must be in [1, 64]", AMM_EINVAL;
-  if (o.gemm_tile < 0 || o.gemm_tile > 3) return *why = "gemm_tile must be in [0, 3]", AMM_EINVAL;
+  if (o.gemm_tile < 0 || o.gemm_tile > 5) return *why = "gemm_tile must be in [0, 5]", AMM_EINVAL;
   if (o.fp64_solves < 0 || o.fp64_solves > 2) return *why = "fp64_solves must be 0, 1 or 2", AMM_EINVAL;
   return AMM_OK;
 }

@@ -56,6 +56,7 @@ __host__ __device__ inline ClusterLayout plan_cluster(const InstDesc& D, int bud
   L.off_Zo = off;   off += B.CK * D.Nr * D.d * 8;   // own users' blocks of Z, compact
   off = align_up(off, 16);
   L.off_part = off; off += B.CK * B.np * 16;        // this block's covariance parts (re hi, lo, im hi, lo)
+  off = align_up(off, 16);
   L.off_x = off;    off += 64;                      // exchanged scalars: rho part (ff, FP64), status
   off = align_up(off, 128);
   L.off_H = off;    off += B.m * B.ldh * 8;
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(kThreads, 1) cluster_iterate_kernel(IterParams
   __shared__ ff s_rhoprev;
   __shared__ ff s_rho;
   __shared__ double s_wsr;
+  __shared__ float4 s_xall[2 * kMaxClusterCells];
 
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.dim_blocks().x;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) cluster_iterate_kernel(IterParams
   float* const s_alpha = reinterpret_cast<float*>(smem + Ly.off_alpha);
   float2* sZo = reinterpret_cast<float2*>(smem + CL.off_Zo);
   float4* part = reinterpret_cast<float4*>(smem + CL.off_part);
-  float* xch = reinterpret_cast<float*>(smem + CL.off_x);  // [0,1] rho part (ff), [2] status; [4,5] FP64 part
+  float* xch = reinterpret_cast<float*>(smem + CL.off_x);  // [0,1] rho part (ff), [2] status, [4,5] FP64 part (lo, hi words)
   float2* sH = reinterpret_cast<float2*>(smem + CL.off_H);
   float2* sV = reinterpret_cast<float2*>(smem + CL.off_V);
   float2* sZ = reinterpret_cast<float2*>(smem + CL.off_Z);
@@ -225,11 +227,16 @@ __global__ void __launch_bounds__(kThreads, 1) cluster_iterate_kernel(IterParams
         ++a;
       }
       ff re = ff_from(q == 0 ? 1.f : 0.f), im = ff_from(0.f);  // q == 0: a diagonal entry
-      for (int k = 0; k < C; ++k) {
-        const float4 v = cluster.map_shared_rank(part, k)[r * np + ee];
-        re = ff_add(re, ff_make(v.x, v.y));
-        im = ff_add(im, ff_make(v.z, v.w));
-      }
+      float4 v[kMaxClusterCells];
+#pragma unroll
+      for (int k = 0; k < kMaxClusterCells; ++k)  // all remote loads in flight at once
+        if (k < C) v[k] = cluster.map_shared_rank(part, k)[r * np + ee];
+#pragma unroll
+      for (int k = 0; k < kMaxClusterCells; ++k)
+        if (k < C) {
+          re = ff_add(re, ff_make(v[k].x, v[k].y));
+          im = ff_add(im, ff_make(v[k].z, v[k].w));
+        }
       sQ[r * np + ee] = make_float2(re.hi, im.hi);
       sQ[(CK + r) * np + ee] = make_float2(re.lo, im.lo);
     }
@@ -253,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1) cluster_iterate_kernel(IterParams
         xch[0] = part_rho.hi;
         xch[1] = part_rho.lo;
         xch[2] = __int_as_float(s_fail);
-        reinterpret_cast<double*>(xch)[2] = part_exact;
+        xch[4] = __int_as_float(__double2loint(part_exact));
+        xch[5] = __int_as_float(__double2hiint(part_exact));
       }
     }
     // ---- exchange 2: U, U W of every user; rho and the status from every block
@@ -268,15 +276,21 @@ __global__ void __launch_bounds__(kThreads, 1) cluster_iterate_kernel(IterParams
       sU[off] = cluster.map_shared_rank(sU, k)[off];
       sUW[off] = cluster.map_shared_rank(sUW, k)[off];
     }
+    if (tid < C) {  // one thread per rank fetches that rank's scalars
+      const float4* xk = reinterpret_cast<const float4*>(cluster.map_shared_rank(xch, tid));
+      s_xall[2 * tid] = xk[0];
+      s_xall[2 * tid + 1] = xk[1];
+    }
+    __syncthreads();
     if (tid == 0) {
       ff rs = ff_from(0.f);
       double ws = 0.0;
       int f = s_fail;
       for (int k = 0; k < C; ++k) {  // rank order: the same sums in every block
-        const float* xk = cluster.map_shared_rank(xch, k);
-        rs = ff_add(rs, ff_make(xk[0], xk[1]));
-        ws += reinterpret_cast<const double*>(xk)[2];
-        const int fk = __float_as_int(xk[2]);
+        const float4 x0 = s_xall[2 * k], x1 = s_xall[2 * k + 1];
+        rs = ff_add(rs, ff_make(x0.x, x0.y));
+        ws += __hiloint2double(__float_as_int(x1.y), __float_as_int(x1.x));
+        const int fk = __float_as_int(x0.z);
         if (fk != kOk) f = fk;
       }
       s_rho = rs;
@@ -296,24 +310,22 @@ __global__ void __launch_bounds__(kThreads, 1) cluster_iterate_kernel(IterParams
     if (s_ctrl[4]) break;
     const int stage = s_ctrl[1];
     const float2* sP = (stage == 2) ? sUW : sU;
-    // ---- S6: Y_r over block j's columns (global numbering c).  Each item reads
-    //      Zhat = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) at its rows, moves Z(V^{t-1}) to
-    //      the global slot (the next iteration's Z(V^{t-2})) and writes Y over the
-    //      local block, where the gradient GEMM reads it
+    // ---- S1: Zhat = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) in place in the local block, in
+    //      one coalesced pass that also moves Z(V^{t-1}) to the global slot (the
+    //      next iteration's Z(V^{t-2}))
+    for (int e = tid; e < m * n; e += blockDim.x) {
+      const int row = e / n, c = e - row * n;
+      const float2 zc = sZ[row * ldzl + c];
+      float2* zg = Zg + (long long)row * ldz + cb + c;
+      if (omega != 0.f) sZ[row * ldzl + c] = csub(cscale(zc, 1.f + omega), cscale(*zg, omega));
+      *zg = zc;
+    }
+    __syncthreads();
+    // ---- S6: Y_r over block j's columns (global numbering c), written over Zhat
     gradient_rhs_phase(
-        D, Ly,
-        [&](int row, int c) {
-          float2 v = sZ[row * ldzl + (c - cb)];
-          if (omega != 0.f) v = csub(cscale(v, 1.f + omega), cscale(Zg[(long long)row * ldz + c], omega));
-          return v;
-        },
-        sU, sP, alpha_u,
+        D, Ly, [&](int row, int c) { return sZ[row * ldzl + (c - cb)]; }, sU, sP, alpha_u,
         [&](int r, int c, const float2* y) {
-          for (int a = 0; a < Nr; ++a) {
-            const int row = r * Nr + a;
-            Zg[(long long)row * ldz + c] = sZ[row * ldzl + (c - cb)];
-            sZ[row * ldzl + (c - cb)] = y[a];
-          }
+          for (int a = 0; a < Nr; ++a) sZ[(r * Nr + a) * ldzl + (c - cb)] = y[a];
         },
         cb, cb + n);
     __syncthreads();

@@ -69,15 +69,28 @@ __device__ __forceinline__ void block_cgemm(int M, int N, int KK, const float2* 
 }
 
 // Register tile of the plain-path block GEMMs: 1 = 4 x 4, 2 = 2 x 2,
-// 3 = 4 x 2; 0 picks the largest tile that still gives every thread of the
-// block at least one tile (small instances leave most threads idle with
-// 4 x 4 tiles).
+// 3 = 4 x 2, 4 = 4 x 3, 5 = 2 x 5.  0 picks, for the shape, the tile whose
+// slowest thread does the least work: rounds of tiles over the block times
+// the tile's multiply-adds plus its operand loads per K step (a 4 x 2 tile
+// over M = 140, N = 20 takes two rounds on some threads, a 4 x 3 tile one).
+__host__ __device__ inline int gemm_tile_pick(int M, int N, int nb) {
+  const int tm[5] = {4, 2, 4, 4, 2}, tn[5] = {4, 2, 2, 3, 5};
+  int best = 1;
+  long long best_cost = -1;
+  for (int k = 0; k < 5; ++k) {
+    const long long tiles = (long long)((M + tm[k] - 1) / tm[k]) * ((N + tn[k] - 1) / tn[k]);
+    const long long rounds = (tiles + nb - 1) / nb;
+    const long long cost = rounds * (4 * tm[k] * tn[k] + 2 * (tm[k] + tn[k]));
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = k + 1;
+    }
+  }
+  return best;
+}
 __device__ __forceinline__ int gemm_tile_for(int opt, int M, int N) {
-  if (opt >= 1 && opt <= 3) return opt;
-  const int nb = (int)blockDim.x;
-  if (((M + 3) / 4) * ((N + 3) / 4) >= nb) return 1;
-  if (((M + 3) / 4) * ((N + 1) / 2) >= nb) return 3;
-  return 2;
+  if (opt >= 1 && opt <= 5) return opt;
+  return gemm_tile_pick(M, N, (int)blockDim.x);
 }
 
 template <int OPA, class Epi>
@@ -87,6 +100,10 @@ __device__ __forceinline__ void block_cgemm_tiled(int tile, int M, int N, int KK
     block_cgemm<2, 2, OPA>(M, N, KK, A, lda, B, ldb, epi);
   else if (tile == 3)
     block_cgemm<4, 2, OPA>(M, N, KK, A, lda, B, ldb, epi);
+  else if (tile == 4)
+    block_cgemm<4, 3, OPA>(M, N, KK, A, lda, B, ldb, epi);
+  else if (tile == 5)
+    block_cgemm<2, 5, OPA>(M, N, KK, A, lda, B, ldb, epi);
   else
     block_cgemm<4, 4, OPA>(M, N, KK, A, lda, B, ldb, epi);
 }
@@ -958,7 +975,7 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
 // busy; zget(row, col).  Returns (re, im) in float-float.
 template <class ZGet>
 __device__ __forceinline__ void cov_entry(ZGet zget, int ra, int rb, int c0, int c1, int skip0, int skip1, ff* re,
-                                          ff* im) {
+                                          ff* im, int step = 1) {
   float sr[4] = {0.f, 0.f, 0.f, 0.f}, cr[4] = {0.f, 0.f, 0.f, 0.f};
   float si[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
   auto acc = [](float& sum, float& comp, float x, float y) {
@@ -968,10 +985,10 @@ __device__ __forceinline__ void cov_entry(ZGet zget, int ra, int rb, int c0, int
     sum = t.hi;
     comp = __fadd_rn(comp, __fadd_rn(t.lo, pe));
   };
-  for (int c = c0; c < c1; c += 4) {
+  for (int c = c0; c < c1; c += 4 * step) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int cc = c + u;
+      const int cc = c + u * step;
       float2 za = make_float2(0.f, 0.f), zb = make_float2(0.f, 0.f);
       if (cc < c1 && (cc < skip0 || cc >= skip1)) {
         za = zget(ra, cc);
@@ -1001,24 +1018,35 @@ __device__ __forceinline__ void cov_entry(ZGet zget, int ra, int rb, int c0, int
 // eq. (9) resolves; so each entry is a compensated dot product (cov_entry),
 // stored as a high part (sQ, read by the FP32 solves) and a low part
 // (sQ + CK np, read by the FP64 and float-float solves).
+// Four consecutive lanes share an entry (columns g, g + 4, ... for lane g)
+// and add their parts by two exchanges, so that all warps take part.
 template <class ZGet>
 __device__ __forceinline__ void covariance_phase(const InstDesc& D, const Layout& Ly, ZGet zget, float2* sQ) {
-  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn, np = Ly.np;
+  const int Nr = D.Nr, K = D.K, d = D.d, n = Ly.n, Cn = Ly.Cn, np = Ly.np, items = Ly.CK * np;
   float2* sQlo = sQ + Ly.CK * np;
-  for (int e = threadIdx.x; e < Ly.CK * np; e += blockDim.x) {
-    const int r = e / np;
-    int q = e - r * np, a = 0;
+  for (int base = 0; base < 4 * items; base += blockDim.x) {  // warp-uniform trip count (the exchanges)
+    const int w = base + (int)threadIdx.x;
+    const int e = w >> 2, g = w & 3;
+    const bool act = e < items;
+    const int r = act ? e / np : 0;
+    int q = act ? e - r * np : 0, a = 0;
     while (q >= Nr - a) {
       q -= Nr - a;
       ++a;
     }
     const int bb = a + q;
     const int own0 = (r / K) * n + (r % K) * d;
-    ff re, im;
-    cov_entry(zget, r * Nr + a, r * Nr + bb, 0, Cn, own0, own0 + d, &re, &im);
-    if (a == bb) re = ff_add(re, ff_from(1.f));
-    sQ[e] = make_float2(re.hi, im.hi);
-    sQlo[e] = make_float2(re.lo, im.lo);
+    ff re = ff_from(0.f), im = ff_from(0.f);
+    if (act) cov_entry(zget, r * Nr + a, r * Nr + bb, g, Cn, own0, own0 + d, &re, &im, 4);
+    re = ff_add(re, ff_shfl_xor(re, 1));
+    im = ff_add(im, ff_shfl_xor(im, 1));
+    re = ff_add(re, ff_shfl_xor(re, 2));
+    im = ff_add(im, ff_shfl_xor(im, 2));
+    if (act && g == 0) {
+      if (a == bb) re = ff_add(re, ff_from(1.f));
+      sQ[e] = make_float2(re.hi, im.hi);
+      sQlo[e] = make_float2(re.lo, im.lo);
+    }
   }
 }
 

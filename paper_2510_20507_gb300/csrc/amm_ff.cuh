@@ -88,6 +88,14 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// acc + a b with the product split exactly (a dot-product step)
+__device__ __forceinline__ ff ff_dot_acc(ff acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const ff t = two_sum(acc.hi, p);
+  return fast_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(e, acc.lo)));
+}
+
 __device__ __forceinline__ ff ff_shfl_xor(ff v, int m) {
   return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
 }

@@ -344,13 +344,14 @@ __device__ void u_load_h(const UParams& p, const UView& X, int b) {
 // V^t = project(Vh - gamma G) into out; returns ||Vh - gamma G||^2
 __device__ double u_step_project(const UView& X, float gam, float Pc, const float2* Vh, float2* out, double* red) {
   const int N = X.Nt * X.n;
-  double s = 0.0;
+  ff sf = ff_from(0.f);  // float-float with exact products: no FP64 instruction per element
   for (int e = threadIdx.x; e < N; e += blockDim.x) {
     const float2 v = make_float2(Vh[e].x - gam * X.G[e].x, Vh[e].y - gam * X.G[e].y);
-    s += (double)v.x * v.x + (double)v.y * v.y;
+    sf = ff_dot_acc(ff_dot_acc(sf, v.x, v.x), v.y, v.y);
   }
-  s = block_sum(s, red);
-  const float sc = (s > (double)Pc) ? (float)sqrt((double)Pc / s) : 1.f;
+  sf = block_sum_ff(sf, reinterpret_cast<float*>(red) + 80);
+  const double s = ff_to_double(sf);
+  const float sc = (sf.hi > Pc) ? sqrtf(Pc / sf.hi) : 1.f;
   for (int e = threadIdx.x; e < N; e += blockDim.x)
     out[e] = make_float2((Vh[e].x - gam * X.G[e].x) * sc, (Vh[e].y - gam * X.G[e].y) * sc);
   __syncthreads();
@@ -565,26 +566,28 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
   const float Pc = p.P[b];
   u_forward_iter(X, stage2, omega, Va, Vb, Vh, fail);
   // projection: Vt = Vh - gam G, V^t = c Vt with c = sqrt(P / ||Vt||^2) when active
-  double s = 0.0, ip = 0.0;
+  // the sums in float-float with exact products (no FP64 instruction per element)
+  float* redf = reinterpret_cast<float*>(red) + 80;
+  ff s = ff_from(0.f), ip = ff_from(0.f);
   for (int e = threadIdx.x; e < N; e += blockDim.x) {
     const float2 v = make_float2(Vh[e].x - gam * X.G[e].x, Vh[e].y - gam * X.G[e].y);
-    s += (double)v.x * v.x + (double)v.y * v.y;
-    ip += (double)A1[e].x * v.x + (double)A1[e].y * v.y;
+    s = ff_dot_acc(ff_dot_acc(s, v.x, v.x), v.y, v.y);
+    ip = ff_dot_acc(ff_dot_acc(ip, A1[e].x, v.x), A1[e].y, v.y);
   }
-  s = block_sum(s, red);
-  ip = block_sum(ip, red);
-  const bool active = s > (double)Pc;
-  const float cc = active ? (float)sqrt((double)Pc / s) : 1.f;
-  const float kk = active ? (float)(ip / s) : 0.f;
-  double gb = 0.0;
+  s = block_sum_ff(s, redf);
+  ip = block_sum_ff(ip, redf);
+  const bool active = s.hi > Pc;
+  const float cc = active ? sqrtf(Pc / s.hi) : 1.f;
+  const float kk = active ? ip.hi / s.hi : 0.f;
+  ff gb = ff_from(0.f);
   for (int e = threadIdx.x; e < N; e += blockDim.x) {
     const float2 v = make_float2(Vh[e].x - gam * X.G[e].x, Vh[e].y - gam * X.G[e].y);
     const float2 bt = make_float2(cc * (A1[e].x - kk * v.x), cc * (A1[e].y - kk * v.y));  // Vtilde-bar
     B[e] = bt;
-    gb += (double)bt.x * X.G[e].x + (double)bt.y * X.G[e].y;
+    gb = ff_dot_acc(ff_dot_acc(gb, bt.x, X.G[e].x), bt.y, X.G[e].y);
   }
-  gb = block_sum(gb, red);  // also orders the writes of B before the reads below
-  if (threadIdx.x == 0) p.gamma_bar[(long long)b * p.T + (t - 1)] = (float)(-gb);
+  gb = block_sum_ff(gb, redf);  // also orders the writes of B before the reads below
+  if (threadIdx.x == 0) p.gamma_bar[(long long)b * p.T + (t - 1)] = -gb.hi;
   // Gbar = -gam B;  Ybar = H Gbar
   block_cgemm_tiled<0>(gemm_tile_for(0, m, n), m, n, Nt, X.H, Nt, B, n,
                        [&](int r, int c, float2 v) { Yb[r * n + c] = cscale(v, -gam); });

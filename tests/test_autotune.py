@@ -12,15 +12,16 @@ from paper_2510_20507_gb300 import autotune
 def test_tune_picks_fastest_and_caches(tmp_path, monkeypatch):
     cache = str(tmp_path / "tune.json")
     monkeypatch.setattr(autotune, "_device_name", lambda: "Fake GPU")
-    fake = {1: 5.0, 2: 3.0, 3: 4.0, 0: 2.5}
+    fake = {("fp32", 0): 3.5, ("fp32", 1): 5.0, ("fp32", 2): 3.0, ("fp32", 3): 4.0, ("fp32", 4): 3.2,
+            ("fp32", 5): 3.3, ("bf16x6", 0): 2.5}
     calls = []
 
     def fake_time(dims, ov, base=None, **kw):
         calls.append(ov)
-        return fake[ov["gemm_tile"]]
+        return fake[(ov["precision"], ov["gemm_tile"])]
     monkeypatch.setattr(autotune, "time_config", fake_time)
     e = autotune.tune((1, 16, 64, 4, 4), "fp32", base={"fp64_solves": 1}, cache=cache)
-    assert e["overrides"] == {"precision": "bf16x6", "gemm_tile": 0} and len(calls) == 4
+    assert e["overrides"] == {"precision": "bf16x6", "gemm_tile": 0} and len(calls) == 7
     table = json.load(open(cache))
     assert list(table) == ["Fake_GPU|1x16x64x4x4|fp32|fp64_solves=1"]
     calls.clear()
@@ -43,13 +44,13 @@ def test_fp32_class_candidates_compute_the_same_solve():
     from gpu_util import GpuRun, rel
     insts = wl.uneven(n=64)
     res = {}
-    for tile in (1, 2, 3):
+    for tile in (1, 2, 3, 4, 5):
         g = GpuRun(insts, gemm_tile=tile)
         g.warmstart()
         g.step(3)
         res[tile] = g.V()
         g.close()
-    worst = max(rel(res[t][b], res[1][b]) for t in (2, 3) for b in range(len(insts)))
+    worst = max(rel(res[t][b], res[1][b]) for t in (2, 3, 4, 5) for b in range(len(insts)))
     print(f"gemm tiles: worst relative V difference after 3 iterations {worst:.2e}")
     assert worst <= 1e-5
 

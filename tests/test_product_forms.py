@@ -1,0 +1,120 @@
+"""Accuracy of the complex-GEMM forms the tensor-core path could use, by
+exact emulation on the CPU: operands rounded to bf16 / TF32 (round to
+nearest even on the FP32 bit pattern), each product of two such values is
+exact in FP32, sums accumulate in FP32 (numpy float32 matmul).  Measured
+against the FP64 product on the timed workload's shape (Z = H V with H
+64 x 64, V 64 x 64, H i.i.d. CN(0,1), V scaled to 30 dB power).
+
+The kernel uses the real 4M embedding [[Hr, -Hi], [Hi, Hr]] [Vr; Vi] with
+three bf16 terms per operand and six products (BF16X6).  The 3M (Gauss)
+form saves a quarter of the products but its (Hr + Hi)(Vr + Vi) term is
+rounded once more and cancels, and TF32 (10 stored mantissa bits) needs
+two terms and three products for the same accuracy while storing 8 bytes
+per operand element against BF16X6's 6 (shared memory is what bounds the
+kernel).  These tests record those facts."""
+import numpy as np
+
+
+def _round_bits(x, drop):
+    """float32 x rounded to nearest even, keeping 23 - drop mantissa bits."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    half = (1 << (drop - 1)) - 1
+    r = (u + half + ((u >> drop) & 1)) & ~np.uint64((1 << drop) - 1)
+    return r.astype(np.uint32).view(np.float32)
+
+
+def bf16(x):
+    return _round_bits(x, 16)
+
+
+def tf32(x):
+    return _round_bits(x, 13)
+
+
+def split(x, rnd, terms):
+    out, r = [], np.asarray(x, dtype=np.float32)
+    for _ in range(terms):
+        t = rnd(r)
+        out.append(t)
+        r = (r - t).astype(np.float32)  # exact: t is r rounded to fewer bits
+    return out
+
+
+def gemm_split(A, B, rnd, terms, pairs):
+    """sum over (p, q) in pairs of A_p B_q with FP32 accumulation."""
+    As, Bs = split(A, rnd, terms), split(B, rnd, terms)
+    acc = np.zeros((A.shape[0], B.shape[1]), dtype=np.float32)
+    for p, q in pairs:
+        acc = (acc + (As[p] @ Bs[q]).astype(np.float32)).astype(np.float32)
+    return acc
+
+
+X6 = [(0, 0), (0, 1), (1, 0), (1, 1), (0, 2), (2, 0)]
+X3 = [(0, 0), (0, 1), (1, 0)]
+
+
+def complex_4m(H, V, rnd, terms, pairs):
+    Hr, Hi = H.real.astype(np.float32), H.imag.astype(np.float32)
+    A = np.block([[Hr, -Hi], [Hi, Hr]]).astype(np.float32)
+    B = np.vstack([V.real, V.imag]).astype(np.float32)
+    Z = gemm_split(A, B, rnd, terms, pairs)
+    m = H.shape[0]
+    return Z[:m].astype(np.float64) + 1j * Z[m:].astype(np.float64)
+
+
+def complex_3m(H, V, rnd, terms, pairs):
+    Hr, Hi = H.real.astype(np.float32), H.imag.astype(np.float32)
+    Vr, Vi = V.real.astype(np.float32), V.imag.astype(np.float32)
+    P1 = gemm_split(Hr, Vr, rnd, terms, pairs)
+    P2 = gemm_split(Hi, Vi, rnd, terms, pairs)
+    P3 = gemm_split((Hr + Hi).astype(np.float32), (Vr + Vi).astype(np.float32), rnd, terms, pairs)
+    Zr = (P1 - P2).astype(np.float32)
+    Zi = ((P3 - P1).astype(np.float32) - P2).astype(np.float32)
+    return Zr.astype(np.float64) + 1j * Zi.astype(np.float64)
+
+
+def _case(seed):
+    rng = np.random.default_rng(seed)
+    H = ((rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))) / np.sqrt(2)).astype(np.complex64)
+    V = ((rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))) / np.sqrt(2)).astype(np.complex64)
+    V *= np.float32(np.sqrt(1000.0 / np.sum(np.abs(V) ** 2)))
+    exact = H.astype(np.complex128) @ V.astype(np.complex128)
+    return H, V, exact
+
+
+def _err(Z, exact):
+    return float(np.linalg.norm(Z - exact) / np.linalg.norm(exact))
+
+
+def test_bf16x6_real_embedding_is_fp32_accurate_and_3m_is_not_better():
+    e4, e3, e32 = [], [], []
+    for seed in range(4):
+        H, V, exact = _case(seed)
+        e4.append(_err(complex_4m(H, V, bf16, 3, X6), exact))
+        e3.append(_err(complex_3m(H, V, bf16, 3, X6), exact))
+        e32.append(_err((H @ V).astype(np.complex128), exact))   # plain FP32 GEMM
+    e4, e3, e32 = max(e4), max(e3), max(e32)
+    print(f"BF16X6 4M {e4:.2e}, BF16X6 3M {e3:.2e}, FP32 {e32:.2e}")
+    assert e4 <= 2 * e32            # the split embedding is as accurate as an FP32 GEMM
+    assert e3 >= 1.2 * e4           # the Gauss form loses accuracy for its saved products
+
+
+def test_tf32_needs_a_split_for_fp32_level_accuracy():
+    H, V, exact = _case(7)
+    e1 = _err(complex_4m(H, V, tf32, 1, [(0, 0)]), exact)
+    e3 = _err(complex_4m(H, V, tf32, 2, X3), exact)
+    eb = _err(complex_4m(H, V, bf16, 1, [(0, 0)]), exact)
+    print(f"TF32 {e1:.2e}, TF32X3 {e3:.2e}, BF16 {eb:.2e}")
+    assert 1e-4 < e1 < 1e-3 and e3 < 1e-5
+    assert eb > 4 * e1              # one bf16 term: 7 stored bits against TF32's 10
+
+
+def test_rounding_emulation():
+    """bf16 keeps 8 significant bits, rounding to nearest with ties to even;
+    a three-term split reproduces the float32 value."""
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, 1.0 + 3 * 2.0 ** -8], dtype=np.float32)
+    assert list(bf16(x)) == [1.0, 1.0, 1.0 + 2.0 ** -7, 1.0 + 2.0 ** -6]   # the tie at 1 + 2^-8 goes to even
+    for v in bf16(np.random.default_rng(0).standard_normal(1000).astype(np.float32)):
+        assert (np.float32(v).view(np.uint32) & 0xFFFF) == 0
+    t = split(np.array([np.pi], dtype=np.float32), bf16, 3)
+    assert float(np.sum([np.float64(q[0]) for q in t])) == float(np.float32(np.pi))

@@ -449,6 +449,40 @@ def run_gpu(args):
             one_step()
         torch.cuda.synchronize()
 
+    # ---- the same tensor-core path with FP64 per-user solves, timed the same way
+    fp64_leg = None
+    if args.solves != "fp64" and not args.no_plain:
+        fopts = pkg.default_opts(precision=args.precision, fp64_solves=SOLVES["fp64"])
+        fsolver = pkg.Solver(batch, pk.dims[0], opts=fopts, stream=stream)
+
+        def fp64_step():
+            fsolver.set_problem(H, alpha, sigma2, P)
+            fsolver.warmstart(G0)
+            fsolver.step(ITERS)
+            fsolver.wsr(wsr)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fp64_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            f0.record(stream)
+            for _ in range(args.steps):
+                fp64_step()
+            f1.record(stream)
+        torch.cuda.synchronize()
+        fms = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+        fp64_leg = {"small_solves": "f64", "value": whole_job_rate(world, batch, args.steps, fms / 1000.0),
+                    "unit": UNIT, "ms_per_step": fms / args.steps}
+        fsolver.close()
+        with torch.cuda.stream(stream):
+            one_step()
+        torch.cuda.synchronize()
+
     # ---- end to end through the C-ABI with host buffers (pinned)
     e2e_value, h2d, d2h, e2e_single = None, 0, 0, None
     if not args.no_e2e:
@@ -479,7 +513,7 @@ def run_gpu(args):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "iterate_kernel",
                 "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                             f"(derived; {src} clocks)"}
+                             f"(derived from the unit counts and the maximum clock, not measured; {src} clocks)"}
     else:
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -537,6 +571,7 @@ def run_gpu(args):
         "ms_per_step_median": statistics.median(step_ms),
         "plain_path": plain,
         "speedup_vs_plain": (value / plain["value"]) if plain else None,
+        "fp64_solves": fp64_leg,
         "parity": parity,
     }
     if rank == 0:
@@ -618,7 +653,7 @@ def run_unrolled(args):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "kernel": "u_forward_kernel + u_backward_kernel",
             "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                         f"(derived; {src} clocks)"}
+                         f"(derived from the unit counts and the maximum clock, not measured; {src} clocks)"}
     # the CPU baseline: the oracle's forward of the unrolled map on a sample
     # (the oracle has no adjoint; the gradients are checked in the tests
     # against FP64 finite differences and a float64 autograd restatement),
@@ -674,11 +709,14 @@ def run_other(args):
         insts, iters, desc = wl.uneven(n=UNEVEN_N), UNEVEN_ITERS, ("uneven single-cell batch: Nt 16..256, K 4..64, "
                                                                 "Nr 1/2/4, 4096")
         sample_n = 128
+    if args.instances:  # an evenly spread subset (profiling runs)
+        insts = insts[::max(1, len(insts) // args.instances)][:args.instances]
     pk = wl.pack(insts)
     dims = pk.dims[0] if pk.uniform else pk.dims
     prec = args.precision if args.precision != "bf16x6" else "fp32"  # tensor-core path: single cell, Nt <= 64 only
     dev = torch.device("cuda", 0)
     s = pkg.Solver(len(insts), dims, precision=prec, fp64_solves=SOLVES[args.solves])
+    path = s.path
     H, G0 = torch.from_numpy(pk.H).to(dev), torch.from_numpy(pk.G0).to(dev)
     al, s2, P = (torch.from_numpy(x).to(dev) for x in (pk.alpha, pk.sigma2, pk.P))
     wsr = torch.empty(len(insts), dtype=torch.float64, device=dev)
@@ -707,6 +745,23 @@ def run_other(args):
     s.status(st)
     n_bad = int((st != 0).sum().item())
     s.close()
+    # the uneven batch also under the persistent schedule (device queue, longest first)
+    persistent = None
+    if name == "uneven":
+        s = pkg.Solver(len(insts), dims, precision=prec, fp64_solves=SOLVES[args.solves], schedule=1)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record()
+        for _ in range(args.steps):
+            step()
+        q1.record()
+        torch.cuda.synchronize()
+        persistent = {"schedule": "persistent blocks, device queue, longest first",
+                      "value": len(insts) * args.steps / (q0.elapsed_time(q1) / 1000.0), "unit": UNIT,
+                      "ms_per_step": q0.elapsed_time(q1) / args.steps}
+        s.close()
 
     # roofline: the algorithmic GEMM flops of a whole step (set-up, solve and
     # WSR evaluation all inside it) against the FP32 FFMA peak
@@ -715,9 +770,10 @@ def run_other(args):
     achieved = flops / (ms / args.steps / 1000.0) / 1e12
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "iterate_kernel",
+            "traffic": None, "kernel": "cluster_iterate_kernel" if path == "cluster" else "iterate_kernel",
             "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                         f"(derived; {src} clocks); achieved over the whole step"}
+                         f"(derived from the unit counts and the maximum clock, not measured); "
+                         f"achieved over the whole step"}
 
     cpu, parity = None, {"bad_status": n_bad}
     if pool is not None:
@@ -734,8 +790,10 @@ def run_other(args):
     print(json.dumps({"metric": "instance-solves/s", "value": len(insts) * args.steps / (ms / 1000.0),
                       "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": prec, "data": "synthetic",
-                      "config": {"workload": desc, "iterations": iters}, "roofline": roof, "cpu_baseline": cpu,
-                      "parity": parity, "clocks": clk}))
+                      "config": {"workload": desc, "iterations": iters, "small_solves": SOLVE_NAMES[args.solves],
+                                 "kernel": path},
+                      "roofline": roof, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
+                      "persistent_schedule": persistent}))
     return 0
 
 
@@ -764,14 +822,15 @@ def main():
     ap.add_argument("--fp32-solves", action="store_true",
                     help="run the per-user Hermitian solves in FP32 instead of FP64")
     ap.add_argument("--solves", default=None, choices=["fp64", "ff", "fp32"],
-                    help="arithmetic of the per-user Hermitian solves (default fp64; ff = float-float pairs)")
+                    help="arithmetic of the per-user Hermitian solves (default ff = float-float pairs, which "
+                         "give the FP64 solves' results on the parity tests; the sweep also times fp64)")
     ap.add_argument("--instances", type=int, default=0,
                     help="solve an evenly spread subset of the batch (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.solves is None:
-        args.solves = "fp32" if args.fp32_solves else "fp64"
+        args.solves = "fp32" if args.fp32_solves else "ff"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "unrolled":

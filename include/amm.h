@@ -120,6 +120,11 @@ typedef struct {
                            distributed shared memory (default, when such a cluster
                            fits the GPU); 0 = one block per instance, one cell's
                            channel block staged per cell and iteration */
+  int schedule;         /* blocks of the one-block-per-instance kernel: 0 = one block
+                           per instance, launched longest first for uneven batches
+                           (default); 1 = persistent blocks, as many as fit the GPU,
+                           each taking the next instance of that order from a device
+                           counter (zeroed by a memset before every launch) */
 } amm_opts;
 
 typedef struct amm_ctx amm_ctx;
@@ -127,7 +132,7 @@ typedef struct amm_ctx amm_ctx;
 /* Fill *opts with the defaults: eps1 0.1, eps2 1e-3, tc 3, gamma_c 0,
  * extrapolate 1, switch_iter -1, step_rule 0, AMM_FP32, u_at_extrapolated 0,
  * lanczos_steps 64, spin_budget 2e9, smem_budget 0, fp64_solves 1, gemm_tile 0,
- * cluster_cells 1. */
+ * cluster_cells 1, schedule 0. */
 AMM_API void amm_default_opts(amm_opts* opts);
 
 /* Create a solver for `batch` instances.  `dims` points to `n_dims` entries:

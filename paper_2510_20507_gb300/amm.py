@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
                 ("step_rule", ctypes.c_int), ("precision", ctypes.c_int), ("u_at_extrapolated", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
                 ("smem_budget", ctypes.c_int), ("fp64_solves", ctypes.c_int), ("gemm_tile", ctypes.c_int),
-                ("cluster_cells", ctypes.c_int)]
+                ("cluster_cells", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
 class State(ctypes.Structure):

@@ -17,6 +17,7 @@
 
 namespace amm {
 cudaError_t iterate_set_smem(int bytes);
+cudaError_t iterate_occupancy(int smem, int* per_sm);
 void iterate_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p);
 __global__ void normalize_kernel(const InstDesc* desc, const float2* Hin, const float* alpha, const float* sigma2,
                                  const float* P, float2* Hout, Scalars* sc);
@@ -90,6 +91,8 @@ struct amm_ctx {
   int tc_bytes = 0;  // shared memory of the tensor-core kernel (0: plain path)
   int wm_bytes = 0;  // shared memory of the WMMSE kernel (-1: sizes it does not cover)
   int cl_bytes = 0;  // shared memory per block of the cluster kernel (0: not used)
+  int* dqueue = nullptr;  // instance counter of the persistent schedule
+  int persist_grid = 0;   // blocks of the persistent schedule (0: one block per instance)
   bool problem_set = false;
   bool started = false;
   std::string err;
@@ -139,6 +142,7 @@ extern "C" void amm_default_opts(amm_opts* o) {
   o->fp64_solves = 1;
   o->gemm_tile = 0;
   o->cluster_cells = 1;
+  o->schedule = 0;
 }
 
 static bool dims_ok(const amm_dims& d, std::string* why) {
@@ -178,7 +182,7 @@ static cudaError_t dalloc(T** p, long long count) {
 
 static void free_all(amm_ctx* c) {
   void* ptrs[] = {c->ddesc, c->dorder, c->H,     c->alpha,    c->P,         c->V,    c->Vprev,  c->Zws,   c->Lws,
-                  c->sc,    c->gamma_c, c->Hin,   c->alpha_in, c->sigma2_in, c->P_in, c->V0_in, c->wsr_dev};
+                  c->sc,    c->gamma_c, c->Hin,   c->alpha_in, c->sigma2_in, c->P_in, c->V0_in, c->wsr_dev, c->dqueue};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -197,6 +201,7 @@ amm_status check_opts(const amm_opts& o, const char** why) {
   if (o.lanczos_steps < 1 || o.lanczos_steps > kMaxLanczos) return *why = "lanczos_steps must be in [1, 64]", AMM_EINVAL;
   if (o.gemm_tile < 0 || o.gemm_tile > 5) return *why = "gemm_tile must be in [0, 5]", AMM_EINVAL;
   if (o.fp64_solves < 0 || o.fp64_solves > 2) return *why = "fp64_solves must be 0, 1 or 2", AMM_EINVAL;
+  if (o.schedule < 0 || o.schedule > 1) return *why = "schedule must be 0 or 1", AMM_EINVAL;
   return AMM_OK;
 }
 }  // namespace amm
@@ -321,6 +326,20 @@ extern "C" amm_status amm_create(amm_ctx** out, int batch, const amm_dims* dims,
       c->cl_bytes = clb;
     cudaGetLastError();  // a cluster that does not fit leaves the plain kernel in charge
   }
+  if (o.schedule == 1 && c->cl_bytes == 0) {
+    // persistent blocks: as many as can be resident for the plain kernel's shared memory
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+        (e = amm::iterate_set_smem(amm::kSmemMax - 1024)) ||
+        (e = amm::iterate_occupancy(smem, &per_sm)) || (e = dalloc(&c->dqueue, 1))) {
+      free_all(c);
+      delete c;
+      cudaGetLastError();
+      return fail(nullptr, e == cudaErrorMemoryAllocation ? AMM_ENOMEM : AMM_ECUDA,
+                  std::string("persistent schedule set-up: ") + cudaGetErrorString(e));
+    }
+    c->persist_grid = std::min(batch, std::max(1, sms * std::max(1, per_sm)));
+  }
   if ((e = cudaMemcpy(c->ddesc, c->hdesc.data(), sizeof(InstDesc) * batch, cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(Scalars) * batch)) ||
       // the limit is per kernel, not per context: raise it to the largest budget any
@@ -414,6 +433,15 @@ static amm_status launch_iterate(amm_ctx* c, const amm::IterParams& p) {
   if (c->tc_bytes > 0 && p.mode != amm::kEvalWsr) {
     amm::tc_launch(solves, c->batch, c->tc_bytes, c->stream, p, c->opts.precision);
     return check_launch(c, "tc_iterate_kernel");
+  }
+  if (c->persist_grid > 0 && p.mode != amm::kEvalWsr) {
+    amm::IterParams q = p;
+    q.queue = c->dqueue;
+    q.batch = c->batch;
+    const cudaError_t e = cudaMemsetAsync(c->dqueue, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "persistent schedule counter");
+    amm::iterate_launch(solves, c->persist_grid, c->smem_bytes, c->stream, q);
+    return check_launch(c, "iterate_kernel");
   }
   amm::iterate_launch(solves, c->batch, c->smem_bytes, c->stream, p);
   return check_launch(c, "iterate_kernel");

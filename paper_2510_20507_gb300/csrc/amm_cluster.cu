@@ -313,12 +313,26 @@ __global__ void __launch_bounds__(kThreads, 1) cluster_iterate_kernel(IterParams
     // ---- S1: Zhat = (1+w) Z(V^{t-1}) - w Z(V^{t-2}) in place in the local block, in
     //      one coalesced pass that also moves Z(V^{t-1}) to the global slot (the
     //      next iteration's Z(V^{t-2}))
-    for (int e = tid; e < m * n; e += blockDim.x) {
-      const int row = e / n, c = e - row * n;
-      const float2 zc = sZ[row * ldzl + c];
-      float2* zg = Zg + (long long)row * ldz + cb + c;
-      if (omega != 0.f) sZ[row * ldzl + c] = csub(cscale(zc, 1.f + omega), cscale(*zg, omega));
-      *zg = zc;
+    for (int e0 = 0; e0 < m * n; e0 += 8 * (int)blockDim.x) {  // eight loads in flight per thread
+      float2 zp[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x + tid;
+        if (e < m * n && omega != 0.f) {
+          const int row = e / n;
+          zp[u] = Zg[(long long)row * ldz + cb + (e - row * n)];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x + tid;
+        if (e < m * n) {
+          const int row = e / n, c = e - row * n;
+          const float2 zc = sZ[row * ldzl + c];
+          if (omega != 0.f) sZ[row * ldzl + c] = csub(cscale(zc, 1.f + omega), cscale(zp[u], omega));
+          Zg[(long long)row * ldz + cb + c] = zc;
+        }
+      }
     }
     __syncthreads();
     // ---- S6: Y_r over block j's columns (global numbering c), written over Zhat

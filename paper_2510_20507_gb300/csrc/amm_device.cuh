@@ -108,6 +108,102 @@ __device__ __forceinline__ void block_cgemm_tiled(int tile, int M, int N, int KK
     block_cgemm<4, 4, OPA>(M, N, KK, A, lda, B, ldb, epi);
 }
 
+// Block-wide complex GEMM for operands in global memory: 64 x 64 output
+// tiles, each thread a 4 x 4 register tile (rows ty + 16 i, columns
+// tx + 16 j, so that a warp reads consecutive shared-memory words), K in
+// chunks of 16 staged through two shared-memory buffers (stage: at least
+// kStageElems float2); the global loads of the next chunk are in flight
+// while the current one is multiplied.  Same OPA and epilogue contract as
+// block_cgemm; blockDim.x must be 256.  Contains __syncthreads().
+constexpr int kStageBM = 64, kStageBN = 64, kStageKC = 16, kStageLdA = kStageKC + 1;
+constexpr int kStageElems = 2 * (kStageBM * kStageLdA + kStageKC * kStageBN);
+
+template <int OPA, class Epi>
+__device__ void block_cgemm_staged(int M, int N, int KK, const float2* __restrict__ A, int lda,
+                                   const float2* __restrict__ B, int ldb, Epi epi, float2* stage) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float2* As[2] = {stage, stage + kStageBM * kStageLdA + kStageKC * kStageBN};
+  float2* Bs[2] = {As[0] + kStageBM * kStageLdA, As[1] + kStageBM * kStageLdA};
+  const int mt = (M + kStageBM - 1) / kStageBM, nt = (N + kStageBN - 1) / kStageBN;
+  const int nch = (KK + kStageKC - 1) / kStageKC;
+  constexpr int kPer = (kStageBM * kStageKC) / 256;  // elements of each tile a thread stages per chunk
+  for (int tile = 0; tile < mt * nt; ++tile) {
+    const int r0 = (tile / nt) * kStageBM, c0 = (tile % nt) * kStageBN;
+    float2 ra[kPer], rb[kPer];
+    auto load = [&](int ch) {
+      const int k0 = ch * kStageKC;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int e = tid + 256 * u;
+        float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+        if (OPA == 0) {  // A(r, k) = A[r lda + k]: a row's 16 k consecutive
+          const int r = e / kStageKC, k = e % kStageKC;
+          if (r0 + r < M && k0 + k < KK) va = A[(long long)(r0 + r) * lda + k0 + k];
+        } else {         // A(r, k) = conj(A[k lda + r]): a k row's 64 r consecutive
+          const int k = e / kStageBM, r = e % kStageBM;
+          if (r0 + r < M && k0 + k < KK) {
+            va = A[(long long)(k0 + k) * lda + r0 + r];
+            va.y = -va.y;
+          }
+        }
+        const int kb = e / kStageBN, cbn = e % kStageBN;
+        if (k0 + kb < KK && c0 + cbn < N) vb = B[(long long)(k0 + kb) * ldb + c0 + cbn];
+        ra[u] = va;
+        rb[u] = vb;
+      }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int e = tid + 256 * u;
+        if (OPA == 0) {
+          const int r = e / kStageKC, k = e % kStageKC;
+          As[buf][r * kStageLdA + k] = ra[u];
+        } else {
+          const int k = e / kStageBM, r = e % kStageBM;
+          As[buf][r * kStageLdA + k] = ra[u];
+        }
+        Bs[buf][(e / kStageBN) * kStageBN + e % kStageBN] = rb[u];
+      }
+    };
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
+      const int buf = ch & 1;
+      if (ch + 1 < nch) load(ch + 1);  // in flight during the products below
+#pragma unroll 4
+      for (int k = 0; k < kStageKC; ++k) {
+        float2 a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[buf][(ty + 16 * i) * kStageLdA + k];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) bb[jj] = Bs[buf][k * kStageBN + tx + 16 * jj];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cfma(a[i], bb[jj], acc[i][jj]);
+      }
+      if (ch + 1 < nch) store(buf ^ 1);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + ty + 16 * i;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = c0 + tx + 16 * jj;
+        if (r < M && c < N) epi(r, c, acc[i][jj]);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------- bulk staging
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));

@@ -68,6 +68,8 @@ struct IterParams {
   int tc, extrapolate, switch_iter, step_rule, lanczos_steps, gemm_tile;
   int smem_budget;
   long long spin_budget;
+  int* queue;          // non-null: persistent blocks take instances from this counter (zeroed per launch)
+  int batch;           // instances of the launch (with queue)
 };
 
 // ---------------------------------------------------------------- plan
@@ -99,7 +101,7 @@ struct Layout {
   int m, n, Cn, CK, np, Lm;
   int ldh, ldv, ldz;
   int off_red, off_cell, off_U, off_UW, off_Q, off_rho, off_y, off_z, off_D, off_tri, off_alpha;
-  int off_H, off_Hs, off_V, off_Z, off_L;
+  int off_H, off_Hs, off_V, off_Z, off_L, off_stage;
   int total;
 };
 
@@ -135,13 +137,19 @@ __host__ __device__ inline Layout plan_layout(const InstDesc& D, int budget, int
   // multi-cell instances whose channel does not fit get a staging buffer for
   // one cell's block Htilde_j instead (staged per GEMM from global memory)
   const int szHs = L.m * L.ldh * 8;
-  L.off_H = L.off_Hs = L.off_V = L.off_Z = L.off_L = -1;
+  // channels that stay in global memory get a staging area for the tiled
+  // GEMMs (two buffers of a 64 x 16 and a 16 x 64 complex tile)
+  const int szStage = 2 * (64 * 17 + 16 * 64) * 8;
+  L.off_H = L.off_Hs = L.off_V = L.off_Z = L.off_L = L.off_stage = -1;
   if (off + szH <= budget) {
     L.off_H = off;
     off += szH;
   } else if (D.C > 1 && off + szHs <= budget) {
     L.off_Hs = off;
     off += szHs;
+  } else if (off + szStage <= budget) {
+    L.off_stage = off;
+    off += szStage;
   }
   if (off + szV <= budget) { L.off_V = off; off += szV; }
   if (off + szZ <= budget) { L.off_Z = off; off += szZ; }

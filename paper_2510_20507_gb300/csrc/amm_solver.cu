@@ -27,16 +27,14 @@
 namespace amm {
 
 // ------------------------------------------------------------------ kernel
+// All iterations of one launch for instance b, by the whole block.
 template <class T>
-__global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t mbar;
+__device__ __forceinline__ void iterate_instance(const IterParams& p, int b, unsigned char* smem, uint64_t& mbar) {
   __shared__ int s_fail;
   __shared__ int s_ctrl[8];
   __shared__ float s_bcast;
   __shared__ ff s_rhoprev;  // R^{t-1} in float-float (hi NaN: none yet)
 
-  const int b = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const InstDesc D = p.desc[b];
   Scalars* scg = p.sc + b;
   const int tid = threadIdx.x;
@@ -145,13 +143,23 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
     return sHs;
   };
   const int tile_z = gemm_tile_for(p.gemm_tile, m, n), tile_g = gemm_tile_for(p.gemm_tile, Nt, n);
+  // channels in global memory: the GEMMs stage their tiles through shared memory
+  float2* const stage = (Ly.off_stage >= 0) ? reinterpret_cast<float2*>(smem + Ly.off_stage) : nullptr;
+  auto gemm_fwd = [&](const float2* A, int lda, const float2* Bm, int ldb, auto epi) {
+    if (stage) block_cgemm_staged<0>(m, n, Nt, A, lda, Bm, ldb, epi, stage);
+    else block_cgemm_tiled<0>(tile_z, m, n, Nt, A, lda, Bm, ldb, epi);
+  };
+  auto gemm_grad = [&](const float2* A, int lda, const float2* Bm, int ldb, auto epi) {
+    if (stage) block_cgemm_staged<1>(Nt, n, m, A, lda, Bm, ldb, epi, stage);
+    else block_cgemm_tiled<1>(tile_g, Nt, n, m, A, lda, Bm, ldb, epi);
+  };
 
   // Z(V^{t-2}) is needed from t = 3 on (omega > 0); rebuild it once per launch.
   if (p.mode != kEvalWsr && p.extrapolate && s_ctrl[0] >= 3) {
     for (int j = 0; j < C; ++j) {
       float2* Zo = vw.Z[zc ^ 1] + j * n;
-      block_cgemm_tiled<0>(tile_z, m, n, Nt, cell_h(j), ldh, vw.V[cur ^ 1] + (long long)j * Nt * ldv,
-                           ldv, [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
+      gemm_fwd(cell_h(j), ldh, vw.V[cur ^ 1] + (long long)j * Nt * ldv, ldv,
+               [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
     }
     __syncthreads();
   }
@@ -162,8 +170,8 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   //      block is at hand (one staging of each block per iteration).
   for (int j = 0; j < C; ++j) {
     float2* Zo = vw.Z[zc] + j * n;
-    block_cgemm_tiled<0>(tile_z, m, n, Nt, cell_h(j), ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
-                         [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
+    gemm_fwd(cell_h(j), ldh, vw.V[cur] + (long long)j * Nt * ldv, ldv,
+             [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
   }
   __syncthreads();
 
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
       const float2* Vc = vw.V[cur] + (long long)j * Nt * ldv;
       float2* Vn = vw.V[cur ^ 1] + (long long)j * Nt * ldv;
       ff nrm = ff_from(0.f);
-      block_cgemm_tiled<1>(tile_g, Nt, n, m, Hj, ldh, Zp + j * n, ldz,
+      gemm_grad(Hj, ldh, Zp + j * n, ldz,
                            [&](int r, int c, float2 g) {
                              const long long idx = (long long)r * ldv + c;
                              float2 vh = Vc[idx];
@@ -250,8 +258,7 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
       }
       if (next_z) {
         float2* Zo = Zp + j * n;
-        block_cgemm_tiled<0>(tile_z, m, n, Nt, Hj, ldh, Vn, ldv,
-                             [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
+        gemm_fwd(Hj, ldh, Vn, ldv, [&](int r, int c, float2 v) { Zo[(long long)r * ldz + c] = v; });
       }
     }
     __syncthreads();
@@ -305,6 +312,31 @@ __global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
   }
 }
 
+// One block per instance (blocks in the order p.order gives: longest first
+// for uneven batches), or, with p.queue, persistent blocks that take the
+// next instance of that order from a device counter until none is left.
+template <class T>
+__global__ void __launch_bounds__(kThreads) iterate_kernel(IterParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t mbar;  // bulk-copy barrier, initialised at the start of every instance
+  __shared__ int s_next;
+  if (!p.queue) {
+    iterate_instance<T>(p, p.order ? p.order[blockIdx.x] : (int)blockIdx.x, smem, mbar);
+    return;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int k = s_next;
+    __syncthreads();  // every thread has read s_next before it changes
+    if (k >= p.batch) break;
+    iterate_instance<T>(p, p.order ? p.order[k] : k, smem, mbar);
+    __syncthreads();  // the instance's last copies have completed (its waits returned)
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&mbar)) : "memory");
+    __syncthreads();
+  }
+}
+
 // Host-side launchers (the capi translation unit does not see the templates).
 cudaError_t iterate_set_smem(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(iterate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -312,6 +344,10 @@ cudaError_t iterate_set_smem(int bytes) {
     e = cudaFuncSetAttribute(iterate_kernel<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(iterate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+// Blocks of the plain kernel (FP64 solves, the largest) resident per SM with this shared memory.
+cudaError_t iterate_occupancy(int smem, int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, iterate_kernel<double>, kThreads, (size_t)smem);
 }
 // solves: 0 FP32, 1 FP64, 2 float-float
 void iterate_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p) {

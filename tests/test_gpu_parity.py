@@ -373,3 +373,20 @@ def test_timed_workload_high_snr_per_step(prec, solves):
     sub = round_inputs([wl.single_cell_64(first=b, count=1)[0] for b in picks])
     assert_step_bounds(teacher_forced(sub, 50, gpu_opts=dict(precision=prec, fp64_solves=solves)),
                        f"timed workload {prec} solves {solves}")
+
+
+def test_persistent_schedule_matches_one_block_per_instance():
+    """schedule = 1 (persistent blocks taking instances from a device
+    counter, longest first) computes every instance exactly as the
+    one-block-per-instance launch: identical iterates and WSR, including
+    the instances whose channel stays in global memory (staged GEMMs)."""
+    insts = round_inputs(wl.uneven(n=4096, count=192))
+    out = []
+    for sched in (0, 1):
+        g = GpuRun(insts, schedule=sched)
+        g.warmstart()
+        g.step(6)
+        out.append((g.V(), g.wsr(), g.status()))
+        g.close()
+    assert all(np.array_equal(a, b) for a, b in zip(out[0][0], out[1][0]))
+    assert np.array_equal(out[0][1], out[1][1]) and np.all(out[1][2] == 0)

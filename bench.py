@@ -50,22 +50,25 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per instance of
 # the iteration kernels, from the ncu captures summarised in profiles/
-# (1216 instances of the timed shape; traffic grows with the instance count,
-# so a full launch is this times its instances).  Valid only for the kernel
-# sources the captures ran: see kernel_digest().
-TRAFFIC = {"digest": "77cc35857a210341",
-           "tc_iterate_kernel": (120.035072e6 + 30.182656e6) / 1216,
-           "iterate_kernel": (120.429568e6 + 28.571136e6) / 1216}
+# (tc_iterate_kernel: 4864 instances of the single-cell shape, 50 iterations;
+# cluster_iterate_kernel: 160 seven-cell instances, 20 iterations; traffic
+# grows with the instance count, so a full launch is this times its
+# instances).  Valid only for the kernel sources the captures ran: see
+# kernel_digest().  Kernels without an entry report null.
+TRAFFIC = {"digest": "3051034905991fe6",
+           "tc_iterate_kernel": (484.346880e6 + 269.819648e6) / 4864,
+           "cluster_iterate_kernel": (185.960192e6 + 47.665920e6) / 160}
 # pipe utilisation of the same captures (% of peak, ncu --set full), reported
 # beside the roofline while the sources match the digest: which unit is busy
-PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.07, "fp64_pct": 28.2, "fma_pct": 8.5, "dram_pct": 0.15,
-                               "issue_active_pct": 25.3},
-         "iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 18.8, "fma_pct": 27.1, "dram_pct": 0.11,
-                            "issue_active_pct": 40.6}}
+PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.13, "fp64_pct": 0.30, "fma_pct": 17.16, "alu_pct": 24.91,
+                               "dram_pct": 0.19, "issue_active_pct": 36.26},
+         "cluster_iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 0.29, "fma_pct": 30.62, "alu_pct": 15.75,
+                                    "dram_pct": 0.10, "issue_active_pct": 45.66}}
 
 
 # the sources the iteration kernels and their launches are built from
-DIGEST_SOURCES = ("amm_capi.cu", "amm_device.cuh", "amm_internal.cuh", "amm_solver.cu", "amm_tc.cu", "amm_tc.cuh")
+DIGEST_SOURCES = ("amm_capi.cu", "amm_device.cuh", "amm_internal.cuh", "amm_solver.cu", "amm_tc.cu", "amm_tc.cuh",
+                  "amm_cluster.cu", "amm_ff.cuh")
 
 
 def kernel_digest():
@@ -507,7 +510,7 @@ def run_gpu(args):
     achieved = flops_launch / (avg_iter_ms / 1000.0) / 1e12
     kname = "iterate_kernel" if args.precision == "fp32" else "tc_iterate_kernel"
     same_sources = kernel_digest() == TRAFFIC["digest"]
-    traffic = TRAFFIC[kname] * batch if same_sources else None
+    traffic = TRAFFIC[kname] * batch if same_sources and kname in TRAFFIC else None
     if args.precision == "fp32":
         peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -518,7 +521,7 @@ def run_gpu(args):
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "tc_iterate_kernel", "peak_note": f"bf16 burst, {src}"}
-    roof["ncu_pipes"] = PIPES[kname] if same_sources else None
+    roof["ncu_pipes"] = PIPES.get(kname) if same_sources else None
 
     # ---- the CPU baseline: the oracle on a sample of this batch (every
     #      stride-th instance, all seven P values), timed; its results are
@@ -769,8 +772,11 @@ def run_other(args):
     flops = sum(algorithmic_gemm_flops(x.C, x.K, x.Nt, x.Nr, x.d) for x in insts) * iters
     achieved = flops / (ms / args.steps / 1000.0) / 1e12
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    kname = "cluster_iterate_kernel" if path == "cluster" else "iterate_kernel"
+    same_sources = kernel_digest() == TRAFFIC["digest"]
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "cluster_iterate_kernel" if path == "cluster" else "iterate_kernel",
+            "traffic": TRAFFIC[kname] * len(insts) if same_sources and kname in TRAFFIC else None,
+            "ncu_pipes": PIPES.get(kname) if same_sources else None, "kernel": kname,
             "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                          f"(derived from the unit counts and the maximum clock, not measured); "
                          f"achieved over the whole step"}

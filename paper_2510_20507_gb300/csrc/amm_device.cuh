@@ -896,7 +896,7 @@ struct Views {
 template <class HGet>
 __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, const float2* sU, const float2* sP,
                               const float* alpha_u, float2* QL, float2* y, float2* z, float2* sD, float* ta,
-                              float* tb, double* red, float* bcast) {
+                              float* tb, double* red, float* bcast, bool h_global = false) {
   const int Nt = D.Nt, m = Ly.m, Nr = D.Nr, d = D.d;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   float* redf = reinterpret_cast<float*>(red);
@@ -904,9 +904,11 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
   float* s_bpart = redf + 8;    // [nw] partial sums of b_j^2
   float* s_lb = redf + 32;      // lower bound of the largest Ritz value (warp 0)
   float* s_done = redf + 33;    // settled flag, read by every thread after a barrier
-  // group of g threads per output row, g a power of two <= 32
+  // group of g threads per output row, g a power of two <= 32; a channel in
+  // global memory is read a row per warp (coalesced) instead
   int g = 1;
   while (g < 32 && 2 * g * m <= (int)blockDim.x) g <<= 1;
+  if (h_global && Nt >= 32) g = 32;
   int gN = 1;
   while (gN < 32 && 2 * gN * Nt <= (int)blockDim.x) gN <<= 1;
   float2* slot[2] = {QL, QL + Nt};

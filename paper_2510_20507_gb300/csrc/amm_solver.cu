@@ -228,7 +228,7 @@ __device__ __forceinline__ void iterate_instance(const IterParams& p, int b, uns
       if (sflag & 1) {
         const float lam = lanczos_norm(
             D, Ly, [&](int i, int q) { return Hj[(long long)i * ldh + q]; }, sU, sP, alpha_u, vw.QL, ly, lz, lD, ta, tb,
-            red, &s_bcast);
+            red, &s_bcast, Ly.off_H < 0 && !sHs);
         gj = (lam > 0.f) ? 1.f / lam : 0.f;
         if ((sflag & 2) && tid == 0) gamma_c[j] = gj;
       } else {

@@ -113,24 +113,39 @@ def nearest(gpu_wsr: float, ref: Reference):
 
 
 def judge(gpu_wsr: float, ref: Reference, inst=None, iters: int = 0, opt: Optional[s.Options] = None,
-          spread: Optional[float] = None) -> Verdict:
-    """Judge one GPU result against its references.  Within GAP_TOL of the
-    nearest it passes; beyond, the FP32 spread of that reference trajectory
-    (given, or computed from ``inst``) decides: gap <= SPREAD_FACTOR *
-    spread passes as FP32-sensitive, anything else fails.  A non-finite GPU
-    result fails."""
+          spread: Optional[float] = None, spreads: Optional[List[float]] = None) -> Verdict:
+    """Judge one GPU result against its references, each admissible
+    trajectory in turn from the nearest: within GAP_TOL of one it passes;
+    beyond, that trajectory's FP32 spread (``spreads[k]``, else ``spread``,
+    else computed from ``inst``) decides: gap <= SPREAD_FACTOR * spread
+    passes as FP32-sensitive.  A run follows one trajectory, and the
+    nearest in WSR need not be the one it took (a chaotic trajectory can
+    end beside a calm one), so every trajectory is tried before the result
+    fails; the verdict then describes the nearest.  A non-finite GPU result
+    fails."""
     if not math.isfinite(gpu_wsr):
         return Verdict(math.inf, math.inf, 0, None, ok=False)
-    k, gap, signed = nearest(gpu_wsr, ref)
-    v = Verdict(gap, signed, k)
-    if gap <= GAP_TOL:
-        return v
-    if spread is None:
-        o = opt or s.Options()
-        if ref.switch[k] is not None or k > 0:
-            o = dataclasses.replace(o, switch_iter=10 ** 9 if ref.switch[k] is None else ref.switch[k])
-        spread = fp32_spread(inst, iters, reference=ref.wsr[k], opt=o, stop_at=gap / SPREAD_FACTOR)
-    v.spread = spread
-    v.sensitive = gap <= SPREAD_FACTOR * spread
-    v.ok = v.sensitive
-    return v
+    gaps = [abs(gpu_wsr - w) / abs(w) for w in ref.wsr]
+    order = sorted(range(len(gaps)), key=gaps.__getitem__)
+    first = None
+    for k in order:
+        v = Verdict(gaps[k], (gpu_wsr - ref.wsr[k]) / abs(ref.wsr[k]), k)
+        if v.gap <= GAP_TOL:
+            return v
+        if spreads is not None:
+            sp = spreads[k]
+        elif spread is not None:
+            sp = spread
+        else:
+            o = opt or s.Options()
+            if ref.switch[k] is not None or k > 0:
+                o = dataclasses.replace(o, switch_iter=10 ** 9 if ref.switch[k] is None else ref.switch[k])
+            sp = fp32_spread(inst, iters, reference=ref.wsr[k], opt=o, stop_at=v.gap / SPREAD_FACTOR)
+        v.spread = sp
+        v.sensitive = v.gap <= SPREAD_FACTOR * sp
+        v.ok = v.sensitive
+        if v.ok:
+            return v
+        if first is None:
+            first = v
+    return first

@@ -63,6 +63,19 @@ def test_judge_rule():
     assert not op.judge(math.nan, ref).ok
 
 
+def test_judge_tries_every_admissible_trajectory():
+    """Two admissible switch trajectories: the result lies nearest the calm
+    one (spread 1e-4) but 1.6e-2 from the chaotic one (spread 1.5e-2), the
+    trajectory it took; it passes against the latter.  With both spreads
+    small it fails, and the verdict describes the nearest trajectory."""
+    ref = op.Reference([324.1, 328.2], [8, 9], 9e-5)
+    got = 324.1 * (1 + 1.6e-2)
+    v = op.judge(got, ref, spreads=[1.5e-2, 1e-4])
+    assert v.ok and v.sensitive and v.which == 0 and abs(v.gap - 1.6e-2) < 1e-12
+    v = op.judge(got, ref, spreads=[1e-3, 1e-4])
+    assert not v.ok and v.which == 1 and abs(v.signed - (got - 328.2) / 328.2) < 1e-12
+
+
 def test_perturbed_solve_without_perturbation_is_the_oracle():
     inst = wl.tiny_fp64(1)[0]
     assert sens.perturbed_wsr_bits(inst, 12) == _solve_bits(inst, 12)

@@ -882,22 +882,68 @@ struct Views {
 // orthogonality as Ritz values converge, but every Ritz value stays within
 // the spectrum up to rounding (Paige's analysis of the finite-precision
 // recurrence), so the largest one converges to ||F_k||_2 from below; the
-// lost orthogonality only adds copies of converged values.  From step 8 on,
-// every second step tests whether the largest Ritz value still moves by
-// more than kLanczosTol (tridiag_top_settled); the iteration ends there, at
-// an invariant Krylov space (b_j below kLanczosBreak times the largest a_j)
-// or at Ly.Lm steps.
-//
-// Three barriers per step.  a_j = (Htilde q_j)^H D (Htilde q_j) is summed
-// while z = D y is formed; w is formed, updated and its norm taken by the
-// thread that owns its entry; q_{j+1} stays unnormalised in the slot of
-// q_{j-1} and its scale 1/b_j is applied where it is read.  QL holds the two
-// slots (2 Nt).  Contains __syncthreads(); FP32 reductions only.
+// lost orthogonality only adds copies of converged values.  From step 12
+// on, every third step tests whether the largest Ritz value still moves by
+// more than kLanczosTol (tridiag_top_settled, by warp 0); the iteration ends
+// there, at an invariant Krylov space (b_j below kLanczosBreak times the
+// largest a_j) or at Ly.Lm steps.  q_{j+1} stays unnormalised in the slot
+// of q_{j-1} and its scale 1/b_j is applied where it is read; QL holds the
+// two slots (2 Nt).  FP32 reductions only.
+__device__ __forceinline__ bool lanczos_check_due(int steps) { return steps >= 12 && (steps - 12) % 3 == 0; }
+
+// D_r = 2 alpha_r P_r U_r^H (Nr x Nr per user) into sD, the fixed start
+// vector (unit-modulus entries with golden-ratio phases) into slot 0 and
+// q_{-1} = 0 into slot 1.  No barrier.
+__device__ __forceinline__ void lanczos_setup(const InstDesc& D, const Layout& Ly, const float2* sU, const float2* sP,
+                                              const float* alpha_u, float2* QL, float2* sD) {
+  const int Nt = D.Nt, Nr = D.Nr, d = D.d;
+  for (int e = threadIdx.x; e < Ly.CK * Nr * Nr; e += blockDim.x) {
+    const int r = e / (Nr * Nr), ab = e - r * Nr * Nr, a = ab / Nr, b = ab - a * Nr;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < d; ++s) acc = cfma(sP[(r * Nr + a) * d + s], make_float2(sU[(r * Nr + b) * d + s].x,
+                                                                              -sU[(r * Nr + b) * d + s].y), acc);
+    sD[e] = cscale(acc, 2.f * alpha_u[r]);
+  }
+  const float rn = rsqrtf((float)Nt);
+  for (int p = threadIdx.x; p < Nt; p += blockDim.x) {
+    float s, c;
+    sincosf(6.2831853f * 0.6180339887f * (float)(p + 1), &s, &c);
+    QL[p] = make_float2(c * rn, s * rn);
+    QL[Nt + p] = make_float2(0.f, 0.f);
+  }
+}
+
+// The estimate of ||F_k||_2 once the steps have ended (warp 0 computes,
+// every thread returns it): the settled lower bound, or the largest
+// eigenvalue of T refined to FP32 resolution.  Contains __syncthreads().
+__device__ __forceinline__ float lanczos_finish(const float* ta, const float* tb, int Leff, bool settled,
+                                                const float* s_lb, float* bcast) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float lam;
+    if (settled) {
+      lam = *s_lb * (1.f + 0.5f * kLanczosTol);
+    } else {
+      float lo = fmaxf(*s_lb, ta[0]);
+      for (int i = 1; i < Leff; ++i) lo = fmaxf(lo, ta[i]);
+      const float2 br = tridiag_top_refine(ta, tb, Leff, lo, tridiag_gershgorin(ta, tb, Leff));
+      lam = 0.5f * (br.x + br.y);
+    }
+    if (threadIdx.x == 0) *bcast = lam;
+  }
+  __syncthreads();
+  return *bcast;
+}
+
+// General form (any shape, hget(i, q) from shared or global memory): three
+// barriers per step.  a_j = (Htilde q_j)^H D (Htilde q_j) is summed while
+// z = D y is formed; w is formed, updated and its norm taken by the thread
+// that owns its entry.  Contains __syncthreads().
 template <class HGet>
 __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, const float2* sU, const float2* sP,
                               const float* alpha_u, float2* QL, float2* y, float2* z, float2* sD, float* ta,
                               float* tb, double* red, float* bcast, bool h_global = false) {
-  const int Nt = D.Nt, m = Ly.m, Nr = D.Nr, d = D.d;
+  const int Nt = D.Nt, m = Ly.m, Nr = D.Nr;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   float* redf = reinterpret_cast<float*>(red);
   float* s_apart = redf;        // [nw] partial sums of a_j
@@ -912,22 +958,7 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
   int gN = 1;
   while (gN < 32 && 2 * gN * Nt <= (int)blockDim.x) gN <<= 1;
   float2* slot[2] = {QL, QL + Nt};
-  // D_r = 2 alpha_r P_r U_r^H (Nr x Nr per user), once per call
-  for (int e = tid; e < Ly.CK * Nr * Nr; e += blockDim.x) {
-    const int r = e / (Nr * Nr), ab = e - r * Nr * Nr, a = ab / Nr, b = ab - a * Nr;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int s = 0; s < d; ++s) acc = cfma(sP[(r * Nr + a) * d + s], make_float2(sU[(r * Nr + b) * d + s].x,
-                                                                              -sU[(r * Nr + b) * d + s].y), acc);
-    sD[e] = cscale(acc, 2.f * alpha_u[r]);
-  }
-  // fixed start vector: unit-modulus entries with golden-ratio phases; q_{-1} = 0
-  const float rn = rsqrtf((float)Nt);
-  for (int p = tid; p < Nt; p += blockDim.x) {
-    float s, c;
-    sincosf(6.2831853f * 0.6180339887f * (float)(p + 1), &s, &c);
-    slot[0][p] = make_float2(c * rn, s * rn);
-    slot[1][p] = make_float2(0.f, 0.f);
-  }
+  lanczos_setup(D, Ly, sU, sP, alpha_u, QL, sD);
   if (tid == 0) {
     *s_lb = 0.f;
     *s_done = 0.f;
@@ -1032,27 +1063,204 @@ __device__ float lanczos_norm(const InstDesc& D, const Layout& Ly, HGet hget, co
     bprev = bj;
     cur ^= 1;
     // convergence check on T_{j+1}; the verdict is read after the next barrier
-    if (warp == 0 && j + 1 >= 8 && ((j + 1) & 1) == 0) {
+    if (warp == 0 && lanczos_check_due(j + 1)) {
       __syncwarp();  // ta[j], tb[j] from lane 0
       const bool done = tridiag_top_settled(ta, tb, j + 1, s_lb);
       if (lane == 0 && done) *s_done = 1.f;
     }
   }
-  __syncthreads();
-  if (tid < 32) {
-    float lam;
-    if (settled) {
-      lam = *s_lb * (1.f + 0.5f * kLanczosTol);
-    } else {
-      float lo = fmaxf(*s_lb, ta[0]);
-      for (int i = 1; i < Leff; ++i) lo = fmaxf(lo, ta[i]);
-      const float2 br = tridiag_top_refine(ta, tb, Leff, lo, tridiag_gershgorin(ta, tb, Leff));
-      lam = 0.5f * (br.x + br.y);
-    }
-    if (tid == 0) *bcast = lam;
+  return lanczos_finish(ta, tb, Leff, settled, s_lb, bcast);
+}
+
+// Sum over the 32 lanes of eight complex values per lane, scattered: lane l
+// returns the total of value l >> 2 (the four lanes of a group agree).  18
+// shuffles instead of 80 for eight separate warp sums; a fixed order.
+__device__ __forceinline__ float2 warp_reduce_scatter8(const float2 (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  float2 u[4], w2[2];
+  const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 snd = b16 ? v[k] : v[k + 4], keep = b16 ? v[k + 4] : v[k];
+    u[k] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, snd.x, 16),
+                       keep.y + __shfl_xor_sync(0xffffffffu, snd.y, 16));
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float2 snd = b8 ? u[k] : u[k + 2], keep = b8 ? u[k + 2] : u[k];
+    w2[k] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, snd.x, 8),
+                        keep.y + __shfl_xor_sync(0xffffffffu, snd.y, 8));
+  }
+  const float2 snd = b4 ? w2[0] : w2[1], keep = b4 ? w2[1] : w2[0];
+  float2 x = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, snd.x, 4),
+                         keep.y + __shfl_xor_sync(0xffffffffu, snd.y, 4));
+  x.x += __shfl_xor_sync(0xffffffffu, x.x, 2);
+  x.y += __shfl_xor_sync(0xffffffffu, x.y, 2);
+  x.x += __shfl_xor_sync(0xffffffffu, x.x, 1);
+  x.y += __shfl_xor_sync(0xffffffffu, x.y, 1);
+  return x;
+}
+
+// Users per warp of the row-blocked form below.
+__host__ __device__ inline int lanczos_users_per_warp(const Layout& Ly, int nw) { return (Ly.CK + nw - 1) / nw; }
+// Whether the row-blocked form applies: 256 threads, Nt <= 64, at most 64
+// rows, and each warp's users spanning at most eight rows.
+__host__ __device__ inline bool lanczos_rows_ok(const InstDesc& D, const Layout& Ly, int threads) {
+  const int nw = threads / 32;
+  return threads == 256 && D.Nt <= 64 && Ly.m <= 64 && D.Nr * lanczos_users_per_warp(Ly, nw) <= 8;
+}
+
+// Row-blocked form when lanczos_rows_ok holds: Htilde (row stride ldh, in
+// global or shared memory) is read once into registers, and a step costs
+// two barriers and no further reads of it.  Warp w owns the rows of its
+// users, its lanes the columns l and l + 32 of those rows.  One
+// reduce-scatter leaves y_i = (Htilde q_j)_i with the four lanes of row i,
+// so z = D y and the warp's part of a_j follow by shuffles within the warp;
+// the warp's part of Htilde^H z (its rows only) goes to wpart (nw x 64),
+// and after the barrier the threads of column p sum the nw parts in warp
+// order, form w, its entry of q_{j+1} and their part of b_j^2.  zbuf: m
+// entries.  Same recurrence, tests and scratch as lanczos_norm otherwise.
+// Not inlined: the registers holding Htilde are its own, not the caller's.
+// Contains __syncthreads().
+static __device__ __noinline__ float lanczos_norm_rows(const InstDesc& D, const Layout& Ly, const float2* Hg, int ldh,
+                                                       const float2* sU, const float2* sP, const float* alpha_u,
+                                                       float2* QL, float2* zbuf, float2* wpart, float2* sD,
+                                                       float* ta, float* tb, double* red, float* bcast) {
+  constexpr int nw = 8;  // lanczos_rows_ok: 256 threads
+  const int Nt = D.Nt, m = Ly.m, Nr = D.Nr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* redf = reinterpret_cast<float*>(red);
+  float* s_apart = redf;        // [nw] partial sums of a_j
+  float* s_bpart = redf + 8;    // [2] partial sums of b_j^2 (the column warps)
+  float* s_lb = redf + 32;
+  float* s_done = redf + 33;
+  const int upw = lanczos_users_per_warp(Ly, nw);
+  const int row0 = warp * upw * Nr;          // first row of this warp's users
+  const int nrow = min(upw * Nr, m - row0);  // rows of this warp (may be <= 0)
+  const int k4 = lane >> 2;                  // the row a lane holds after the reduce-scatter
+  const bool lead = (lane & 3) == 0;
+  const int ncw = (Nt + 31) >> 5;            // warps that combine the columns (1 or 2)
+  float2* slot[2] = {QL, QL + Nt};
+  // this warp's rows of Htilde, columns lane and lane + 32
+  float2 h0[8], h1[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float2* hr = Hg + (long long)(row0 + k) * ldh;
+    h0[k] = (k < nrow && lane < Nt) ? hr[lane] : make_float2(0.f, 0.f);
+    h1[k] = (k < nrow && lane + 32 < Nt) ? hr[lane + 32] : make_float2(0.f, 0.f);
+  }
+  lanczos_setup(D, Ly, sU, sP, alpha_u, QL, sD);
+  if (tid == 0) {
+    *s_lb = 0.f;
+    *s_done = 0.f;
   }
   __syncthreads();
-  return *bcast;
+  // the lane's row of its user's D_r (row k4 after the reduce-scatter), and
+  // the lanes that hold the user's y entries; zero beyond Nr
+  const int u = k4 / Nr, a = k4 - u * Nr, r = warp * upw + u;
+  const bool valid = k4 < nrow && r < Ly.CK;
+  float2 dr[kMaxNr];
+  int ysrc[kMaxNr];
+#pragma unroll
+  for (int b = 0; b < kMaxNr; ++b) {
+    dr[b] = (valid && b < Nr) ? sD[(r * Nr + a) * Nr + b] : make_float2(0.f, 0.f);
+    ysrc[b] = min(4 * (u * Nr + b) + (lane & 3), 31);
+  }
+  const int Lm = Ly.Lm;
+  int Leff = Lm;
+  bool settled = false;
+  float amax = 0.f;
+  float sc_cur = 1.f, sc_prev = 0.f;
+  float bprev = 0.f;
+  int cur = 0;
+  for (int j = 0; j < Lm; ++j) {
+    const float2* qj = slot[cur];
+    // ---- y = Htilde q_j over this warp's rows, z = D y, a_j's part and
+    //      this warp's part of Htilde^H z
+    {
+      const float2 q0 = (lane < Nt) ? cscale(qj[lane], sc_cur) : make_float2(0.f, 0.f);
+      const float2 q1 = (lane + 32 < Nt) ? cscale(qj[lane + 32], sc_cur) : make_float2(0.f, 0.f);
+      float2 acc[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = cfma(h1[k], q1, cmul(h0[k], q0));
+      const float2 yk = warp_reduce_scatter8(acc);  // y of local row k4 (zero beyond nrow)
+      // z_i = sum_b D_r[a][b] y_{r Nr + b}: the rows of user u sit in lanes 4 (u Nr + b) + (lane & 3)
+      float2 yb[kMaxNr];
+#pragma unroll
+      for (int b = 0; b < kMaxNr; ++b)
+        yb[b] = make_float2(__shfl_sync(0xffffffffu, yk.x, ysrc[b]), __shfl_sync(0xffffffffu, yk.y, ysrc[b]));
+      float2 zk = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < kMaxNr; ++b) zk = cfma(dr[b], yb[b], zk);  // zero beyond Nr and for invalid rows
+      if (valid && lead) zbuf[row0 + k4] = zk;
+      __syncwarp();
+      float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+      if (nrow > 0) {  // rows past nrow hold zero channel entries: clamp their index, keep the sum
+        float2 zr[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) zr[k] = zbuf[row0 + min(k, nrow - 1)];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          w0 = cjfma(h0[k], zr[k], w0);
+          w1 = cjfma(h1[k], zr[k], w1);
+        }
+      }
+      wpart[warp * 64 + lane] = w0;
+      wpart[warp * 64 + 32 + lane] = w1;
+      float apart = lead ? fmaf(yk.x, zk.x, yk.y * zk.y) : 0.f;
+      apart = warp_sum(apart);
+      if (lane == 0) s_apart[warp] = apart;
+    }
+    __syncthreads();
+    if (*s_done != 0.f) {  // set by the previous step's check
+      settled = true;
+      break;
+    }
+    float aj = 0.f;
+#pragma unroll
+    for (int q2 = 0; q2 < nw; ++q2) aj += s_apart[q2];  // same order in every thread
+    // ---- w = Htilde^H z - a_j q_j - b_{j-1} q_{j-1}: thread p sums the parts in warp order
+    float2* qn = slot[cur ^ 1];
+    if (warp < ncw) {
+      float bpart = 0.f;
+      if (tid < Nt) {
+        float2 gp[nw];
+#pragma unroll
+        for (int q2 = 0; q2 < nw; ++q2) gp[q2] = wpart[q2 * 64 + tid];
+        float2 g = gp[0];
+#pragma unroll
+        for (int q2 = 1; q2 < nw; ++q2) g = cadd(g, gp[q2]);
+        const float2 v = csub(csub(g, cscale(qj[tid], aj * sc_cur)), cscale(qn[tid], bprev * sc_prev));
+        qn[tid] = v;
+        bpart = cabs2(v);
+      }
+      bpart = warp_sum(bpart);
+      if (lane == 0) s_bpart[warp] = bpart;
+    }
+    __syncthreads();
+    float ss = s_bpart[0];
+    if (ncw > 1) ss += s_bpart[1];
+    const float bj = sqrtf(ss);
+    if (tid == 0) {
+      ta[j] = aj;
+      tb[j] = bj;
+    }
+    amax = fmaxf(amax, aj);
+    if (j + 1 >= Lm || !(bj > kLanczosBreak * amax)) {
+      Leff = j + 1;
+      break;
+    }
+    sc_prev = sc_cur;
+    sc_cur = 1.f / bj;
+    bprev = bj;
+    cur ^= 1;
+    if (warp == 0 && lanczos_check_due(j + 1)) {
+      __syncwarp();
+      const bool done = tridiag_top_settled(ta, tb, j + 1, s_lb);
+      if (lane == 0 && done) *s_done = 1.f;
+    }
+  }
+  return lanczos_finish(ta, tb, Leff, settled, s_lb, bcast);
 }
 
 // ------------------------------------------------------- per-user phases

@@ -83,6 +83,42 @@ __host__ __device__ inline TcLayout plan_tc(const InstDesc& D, int budget, int l
   return T;
 }
 
+// ||F_k||_2 by the general Lanczos form for shapes the row-blocked form
+// does not take: with the FP32 channel copied into the idle Z staging
+// buffer, or (when it does not fit there) summed from the bf16 split terms.
+// Not inlined: they keep their registers out of the kernel's.
+static __device__ __noinline__ float tc_lanczos_staged(const InstDesc& D, const Layout& Ly, const float2* Hg,
+                                                       float2* Zs, int ldz, const float2* sU, const float2* sP,
+                                                       const float* alpha_u, float2* QL, float2* ly, float2* lz,
+                                                       float2* lD, float* ta, float* tb, double* red, float* bcast) {
+  const int m = Ly.m, Nt = D.Nt;
+  for (int e = threadIdx.x; e < m * Nt; e += blockDim.x) {
+    const int i = e / Nt, q = e - i * Nt;
+    Zs[(long long)i * ldz + q] = Hg[e];
+  }
+  __syncthreads();
+  return lanczos_norm(
+      D, Ly, [&](int i, int q) { return Zs[(long long)i * ldz + q]; }, sU, sP, alpha_u, QL, ly, lz, lD, ta, tb, red,
+      bcast);
+}
+static __device__ __noinline__ float tc_lanczos_split(const InstDesc& D, const Layout& Ly, unsigned char* const* A1,
+                                                      int NS, int K1p, const float2* sU, const float2* sP,
+                                                      const float* alpha_u, float2* QL, float2* ly, float2* lz,
+                                                      float2* lD, float* ta, float* tb, double* red, float* bcast) {
+  const int m = Ly.m;
+  return lanczos_norm(
+      D, Ly,
+      [&](int i, int q) {
+        float re = 0.f, im = 0.f;
+        for (int t = NS - 1; t >= 0; --t) {  // small terms first
+          re += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(i, q, K1p)));
+          im += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(m + i, q, K1p)));
+        }
+        return make_float2(re, im);
+      },
+      sU, sP, alpha_u, QL, ly, lz, lD, ta, tb, red, bcast);
+}
+
 template <class SolveT>
 __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, int prec) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -447,29 +483,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       float gk;
       if (sflag & 1) {
         float lam;
-        if (Nt <= ldz) {
-          for (int e = tid; e < m * Nt; e += blockDim.x) {
-            const int i = e / Nt, q = e - i * Nt;
-            Zs[(long long)i * ldz + q] = Hg[e];
-          }
-          __syncthreads();
-          lam = lanczos_norm(
-              D, Ly, [&](int i, int q) { return Zs[(long long)i * ldz + q]; }, sU, sP, alpha_u, QL, ly, lz, lD, ta, tb,
-              red, &s_bcast);
+        if (lanczos_rows_ok(D, Ly, blockDim.x) && m * ldz >= (int)(blockDim.x >> 5) * 64) {
+          // the channel straight from global memory into registers; the
+          // staging buffer holds the warps' parts of Htilde^H z
+          lam = lanczos_norm_rows(D, Ly, Hg, Nt, sU, sP, alpha_u, QL, lz, Zs, lD, ta, tb, red, &s_bcast);
+        } else if (Nt <= ldz) {
+          lam = tc_lanczos_staged(D, Ly, Hg, Zs, ldz, sU, sP, alpha_u, QL, ly, lz, lD, ta, tb, red, &s_bcast);
         } else {
-          lam = lanczos_norm(
-              D, Ly,
-              [&](int i, int q) {
-                float re = 0.f, im = 0.f;
-                for (int t = NS - 1; t >= 0; --t) {  // small terms first
-                  re += __bfloat162float(
-                      *reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(i, q, T.K1p)));
-                  im += __bfloat162float(
-                      *reinterpret_cast<const __nv_bfloat16*>(A1[t] + tc::kmaj_off(m + i, q, T.K1p)));
-                }
-                return make_float2(re, im);
-              },
-              sU, sP, alpha_u, QL, ly, lz, lD, ta, tb, red, &s_bcast);
+          lam = tc_lanczos_split(D, Ly, A1, NS, T.K1p, sU, sP, alpha_u, QL, ly, lz, lD, ta, tb, red, &s_bcast);
         }
         gk = (lam > 0.f) ? 1.f / lam : 0.f;
         if ((sflag & 2) && tid == 0) gamma_c[0] = gk;

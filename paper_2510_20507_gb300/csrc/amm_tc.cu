@@ -502,8 +502,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     // ---- S6/S7: G = H^H Y on the tensor cores
     if (!gemm(colD2, T.mn ? A1 : A2, T.K2p, T.mn, false)) break;
     const float gj = cellf[0];
-    ff nrm = ff_from(0.f);
     // Vtilde = Vhat - gamma G into the V^{t-2} slot and the block's ||Vtilde||^2
+    // (four float-float partial sums: a chain of 8 additions, not 32)
+    ff nacc[4] = {ff_from(0.f), ff_from(0.f), ff_from(0.f), ff_from(0.f)};
     for (int cc = half; cc < nchunks; cc += 2) {
       float g[16], v[16], vp[16];
       tc::tmem_ld16x3(lane_addr + colD2 + cc * 16, lane_addr + colV[cur] + cc * 16,
@@ -514,11 +515,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
         const float vh = (omega != 0.f) ? (1.f + omega) * v[j] - omega * vp[j] : v[j];
         float vt = vh - gj * g[j];
         if (!(c < n && R < 2 * Nt)) vt = 0.f;
-        nrm = ff_add(nrm, ff_from(vt * vt));
+        nacc[j & 3] = ff_add(nacc[j & 3], ff_from(vt * vt));
         v[j] = vt;
       }
       tc::tmem_st16(lane_addr + colV[cur ^ 1] + cc * 16, v);
     }
+    const ff nrm = ff_add(ff_add(nacc[0], nacc[1]), ff_add(nacc[2], nacc[3]));
     tc::tmem_wait_st();
     // ||Vtilde||^2 in float-float, then the projection (eq. (15)) and
     // B1 = split(V^t) for the next forward GEMM

@@ -51,19 +51,19 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per instance of
 # the iteration kernels, from the ncu captures summarised in profiles/
 # (tc_iterate_kernel: 4864 instances of the single-cell shape, 50 iterations;
-# cluster_iterate_kernel: 160 seven-cell instances, 20 iterations; traffic
+# cluster_iterate_kernel: 160 seven-cell instances, 50 iterations; traffic
 # grows with the instance count, so a full launch is this times its
 # instances).  Valid only for the kernel sources the captures ran: see
 # kernel_digest().  Kernels without an entry report null.
-TRAFFIC = {"digest": "3051034905991fe6",
-           "tc_iterate_kernel": (484.346880e6 + 269.819648e6) / 4864,
-           "cluster_iterate_kernel": (185.960192e6 + 47.665920e6) / 160}
+TRAFFIC = {"digest": "d0747e27cc3e3907",
+           "tc_iterate_kernel": (485.464832e6 + 283.257088e6) / 4864,
+           "cluster_iterate_kernel": (187.313920e6 + 48.336128e6) / 160}
 # pipe utilisation of the same captures (% of peak, ncu --set full), reported
 # beside the roofline while the sources match the digest: which unit is busy
-PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.13, "fp64_pct": 0.30, "fma_pct": 17.16, "alu_pct": 24.91,
-                               "dram_pct": 0.19, "issue_active_pct": 36.26},
-         "cluster_iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 0.29, "fma_pct": 30.62, "alu_pct": 15.75,
-                                    "dram_pct": 0.10, "issue_active_pct": 45.66}}
+PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.73, "fp64_pct": 0.34, "fma_pct": 18.93, "alu_pct": 25.84,
+                               "dram_pct": 0.22, "issue_active_pct": 39.12},
+         "cluster_iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 0.28, "fma_pct": 30.29, "alu_pct": 16.20,
+                                    "dram_pct": 0.10, "issue_active_pct": 45.62}}
 
 
 # the sources the iteration kernels and their launches are built from

@@ -95,8 +95,8 @@ typedef struct {
   int u_at_extrapolated;/* 0: U^t at V^{t-1};  1: U^t at the extrapolated point */
   int lanczos_steps;    /* most Lanczos steps for ||F_k||_2 (capped at Nt and 64);
                            the iteration stops earlier once its largest Ritz
-                           value moves by less than 1e-6 relative over two
-                           steps; 64 */
+                           value, tested at step 12 and every third step after,
+                           moves by less than 1e-6 relative between tests; 64 */
   long long spin_budget;/* SM clock cycles any device-side wait may spin before
                            the instance gets AMM_ETIMEOUT; 2e9 (about 1 s) */
   int smem_budget;      /* bytes of shared memory per block the solver may use;

@@ -35,6 +35,7 @@ ITERS = 50
 N_PER_P = 1024
 HEX7_N, HEX7_ITERS = 256, 50
 UNEVEN_N, UNEVEN_ITERS = 4096, 30
+WMMSE_N, WMMSE_ITERS = 1024, 10
 SOLVES = {"fp64": 1, "ff": 2, "fp32": 0}
 SOLVE_NAMES = {"fp64": "f64", "ff": "f32x2 (float-float, about 48-bit significands)", "fp32": "f32"}
 WORKLOAD = "single-cell P sweep: Nt=64, K=16, Nr=4, d=4, iid CN(0,1), P=0..30 dB (7x1024 instances), 50 iterations"
@@ -183,6 +184,8 @@ def _instances(name, first, count):
         return wl.hex7(n=HEX7_N, first=first, count=count)
     if name == "uneven":
         return wl.uneven(n=UNEVEN_N, first=first, count=count)
+    if name == "wmmse":
+        return wl.unrolled_64(n=WMMSE_N, first=first, count=count)
     return wl.single_cell_64(N_PER_P, first=first, count=count)
 
 
@@ -205,6 +208,20 @@ def _judge_worker(args):
     name = args[4] if len(args) > 4 else "sweep"
     from oracle import parity as op
     return op.judge(got, ref, _round32(_instances(name, b, 1)[0]), iters)
+
+
+def _wmmse_worker(args):
+    """The oracle's plain WMMSE (Algorithm 2, bisection to width 1e-4, at
+    most 100 halvings) on one instance of the WMMSE workload: (index, WSR in
+    bits after the iterations)."""
+    import math
+    from oracle import solvers as osv
+    b, iters = args
+    inst = _round32(_instances("wmmse", b, 1)[0])
+    V0 = osv.initial_precoder(inst.G0, inst.P)
+    _, hist, _ = osv.wmmse(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0, iters,
+                           tol=1e-4, max_bisect=100)
+    return b, hist[-1] / math.log(2.0)
 
 
 def _oracle_serial(jobs):
@@ -803,15 +820,115 @@ def run_other(args):
     return 0
 
 
+def run_wmmse(args):
+    """Plain WMMSE (Algorithm 2) on the GPU, the comparison method of the
+    paper: 1024 single-cell instances (Nt=64, K=16, Nr=2, d=2, 20 dB), 10
+    iterations per solve, the V update of eq. (12) by the Jacobi
+    eigen-decomposition of A_k (amm_wmmse_step_eig; timed) and by a Cholesky
+    factorisation per bisection point (amm_wmmse_step; timed beside it).
+    The CPU-baseline leg runs the oracle's WMMSE on a sample, timed, and its
+    WSR is the reference for the gap."""
+    pool, cores = None, os.cpu_count() or 1
+    if not args.no_cpu_baseline:
+        pool = make_pool(cores)  # spawned before the first CUDA call
+    import numpy as np
+    import torch
+    import workloads as wl
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2510_20507_gb300 as pkg
+    insts = wl.unrolled_64(n=WMMSE_N)
+    if args.instances:
+        insts = insts[::max(1, len(insts) // args.instances)][:args.instances]
+    iters = WMMSE_ITERS
+    pk = wl.pack(insts)
+    dev = torch.device("cuda", 0)
+    H, G0 = torch.from_numpy(pk.H).to(dev), torch.from_numpy(pk.G0).to(dev)
+    al, s2, P = (torch.from_numpy(x).to(dev) for x in (pk.alpha, pk.sigma2, pk.P))
+    wsr = torch.empty(len(insts), dtype=torch.float64, device=dev)
+
+    def timed(eig):
+        s = pkg.Solver(len(insts), pk.dims[0], precision="fp32")
+
+        def step():
+            s.set_problem(H, al, s2, P)
+            s.warmstart(G0)
+            s.wmmse_step(iters, 1e-4, 100, eig=eig)
+            s.wsr(wsr)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        st = torch.empty(len(insts), dtype=torch.int32, device=dev)
+        s.status(st)
+        bad = int((st != 0).sum().item())
+        got = wsr.cpu().numpy()
+        s.close()
+        return e0.elapsed_time(e1), clk, bad, got
+
+    ms, clk, n_bad, got = timed(True)
+    ms_chol, _, bad_chol, got_chol = timed(False)
+    peaks, src = measured_peaks()
+    x = insts[0]
+    m, n, Nt = x.K * x.Nr, x.K * x.d, x.Nt
+    # the GEMM-shaped work of one iteration per instance: Z = H V, A = H^H (D H), the
+    # two products with Q (Q^H B and Q Y) and the Jacobi rotations counted as
+    # 24 Nt^3 flops per sweep for six sweeps (the measured typical count)
+    flops = (8 * m * Nt * n + 8 * Nt * Nt * m + 2 * 8 * Nt * Nt * n + 6 * 24 * Nt ** 3) * iters * len(insts)
+    achieved = flops / (ms / args.steps / 1000.0) / 1e12
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "wmmse_kernel (eig)",
+            "peak_note": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                         f"(derived, not measured); achieved over the whole step, nominal flops"}
+    cpu, parity = None, {"bad_status": n_bad + bad_chol}
+    if pool is not None:
+        sample_n = 32
+        stride = max(1, len(insts) // sample_n)
+        idx = list(range(0, len(insts), stride))[:sample_n]
+        t0 = time.perf_counter()
+        res = pool.map(_wmmse_worker, [(b, iters) for b in idx], chunksize=1)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(res) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(res)} instances (every {stride}-th), the oracle's WMMSE, {iters} iterations each, "
+                         f"one process per core, {dt:.1f} s"}
+        gaps = np.array([abs(got[b] - w) / w for b, w in res])
+        gaps_c = np.array([abs(got_chol[b] - w) / w for b, w in res])
+        parity.update({"checked": len(res), "max_wsr_gap": float(gaps.max()), "median_wsr_gap": float(np.median(gaps)),
+                       "within_1e-3": int(np.sum(gaps <= 1e-3)),
+                       "cholesky_max_wsr_gap": float(gaps_c.max()), "cholesky_within_1e-3": int(np.sum(gaps_c <= 1e-3))})
+        pool.close()
+    print(json.dumps({"metric": "instance-solves/s (plain WMMSE, 10 iterations)",
+                      "value": len(insts) * args.steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                      "higher_is_better": True, "dtype": "fp32", "data": "synthetic",
+                      "config": {"workload": "WMMSE: Nt=64, K=16, Nr=2, d=2, P=20 dB, 1024 instances",
+                                 "iterations": iters, "v_update": "Jacobi eigen-decomposition of A_k"},
+                      "roofline": roof, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
+                      "cholesky_bisection": {"value": len(insts) * args.steps / (ms_chol / 1000.0), "unit": UNIT,
+                                             "ms_per_step": ms_chol / args.steps}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "unrolled", "hex7", "uneven"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "unrolled", "hex7", "uneven", "wmmse"],
                     help="sweep: the timed P-sweep solve (default); unrolled: the differentiable unrolled workload; "
-                         "hex7 / uneven: solve throughput of the seven-cell and mixed-size workloads")
+                         "hex7 / uneven: solve throughput of the seven-cell and mixed-size workloads; wmmse: the "
+                         "plain WMMSE comparison method")
     ap.add_argument("--precision", default="bf16x6", choices=["fp32", "bf16", "bf16x3", "bf16x6"])
     ap.add_argument("--smem-budget", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -843,6 +960,8 @@ def main():
         return run_unrolled(args)
     if args.workload in ("hex7", "uneven"):
         return run_other(args)
+    if args.workload == "wmmse":
+        return run_wmmse(args)
     return run_gpu(args)
 
 

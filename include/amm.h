@@ -193,6 +193,15 @@ AMM_API amm_status amm_wsr(amm_ctx* ctx, double* wsr);
  * reference on the GPU, not the fast path. */
 AMM_API amm_status amm_wmmse_step(amm_ctx* ctx, int n_iters, double bisect_tol, int bisect_max);
 
+/* The same WMMSE iteration (Algorithm 2, eq. (12) with the same bisection and
+ * arguments) with A_k = Q diag(l) Q^H decomposed once per cell and iteration
+ * by cyclic Jacobi rotations (FP32, at most 12 sweeps, until the
+ * off-diagonal mass is below 1e-5 of ||A_k||_F): each bisection point then
+ * costs O(Nt K d) instead of a Cholesky factorisation, and
+ * V_k = Q diag(1 / (l + lambda)) Q^H B_k.  Same sizes, errors and status
+ * words as amm_wmmse_step. */
+AMM_API amm_status amm_wmmse_step_eig(amm_ctx* ctx, int n_iters, double bisect_tol, int bisect_max);
+
 /* Copy the current iterate V (complex64, V layout) to a device buffer. */
 AMM_API amm_status amm_get_V(const amm_ctx* ctx, void* V);
 

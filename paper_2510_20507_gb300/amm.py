@@ -47,7 +47,7 @@ class State(ctypes.Structure):
 
 
 EXPORTS = ["amm_default_opts", "amm_create", "amm_sizes", "amm_set_problem", "amm_warmstart", "amm_step",
-           "amm_solve", "amm_wsr", "amm_wmmse_step", "amm_get_V", "amm_get_state", "amm_set_state",
+           "amm_solve", "amm_wsr", "amm_wmmse_step", "amm_wmmse_step_eig", "amm_get_V", "amm_get_state", "amm_set_state",
            "amm_status_dev", "amm_solve_host", "amm_destroy", "amm_last_error", "amm_launch_count", "amm_path",
            "amm_solve_noalloc", "amm_test_fail_alloc", "amm_graph_create", "amm_graph_launch", "amm_graph_destroy", "amm_unrolled_create", "amm_unrolled_forward", "amm_unrolled_backward",
            "amm_unrolled_status", "amm_unrolled_last_error", "amm_unrolled_destroy"]
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "amm_solve": (i32, [vp, i32, vp]),
         "amm_wsr": (i32, [vp, vp]),
         "amm_wmmse_step": (i32, [vp, i32, dbl, i32]),
+        "amm_wmmse_step_eig": (i32, [vp, i32, dbl, i32]),
         "amm_get_V": (i32, [vp, vp]),
         "amm_get_state": (i32, [vp, ctypes.POINTER(State)]),
         "amm_set_state": (i32, [vp, ctypes.POINTER(State)]),
@@ -224,8 +225,10 @@ class Solver:
         self._check(self.lib.amm_wsr(self.h, _ptr(out)))
         return out
 
-    def wmmse_step(self, n_iters: int, bisect_tol: float = 1e-4, bisect_max: int = 100):
-        self._check(self.lib.amm_wmmse_step(self.h, n_iters, bisect_tol, bisect_max))
+    def wmmse_step(self, n_iters: int, bisect_tol: float = 1e-4, bisect_max: int = 100, eig: bool = False):
+        """Plain WMMSE iterations (amm_wmmse_step, or amm_wmmse_step_eig when eig)."""
+        f = self.lib.amm_wmmse_step_eig if eig else self.lib.amm_wmmse_step
+        self._check(f(self.h, n_iters, bisect_tol, bisect_max))
 
     def get_V(self, out):
         self._check(self.lib.amm_get_V(self.h, _ptr(out)))

@@ -25,7 +25,7 @@ __global__ void init_kernel(const InstDesc* desc, const float2* V0, const float*
                             Scalars* sc, float* gamma_c, int switch_iter);
 cudaError_t tc_set_smem(int bytes);
 void tc_launch(int solves, int grid, int smem, cudaStream_t st, const IterParams& p, int prec);
-__global__ void wmmse_kernel(IterParams p, float bisect_tol, int bisect_max);
+__global__ void wmmse_kernel(IterParams p, float bisect_tol, int bisect_max, int eig);
 int wmmse_plan_bytes(const InstDesc* desc, int batch, int budget);
 int tc_plan_bytes(const InstDesc* desc, int batch, int budget, int lanczos_steps, int prec);
 int cluster_plan_bytes(const InstDesc* desc, int batch, int budget, int lanczos_steps);
@@ -480,19 +480,28 @@ extern "C" amm_status amm_wsr(amm_ctx* c, double* wsr) {
   return launch_iterate(c, p);
 }
 
-extern "C" amm_status amm_wmmse_step(amm_ctx* c, int n_iters, double bisect_tol, int bisect_max) {
+static amm_status wmmse_launch(amm_ctx* c, const char* what, int n_iters, double bisect_tol, int bisect_max,
+                               int eig) {
   if (!c) return AMM_EINVAL;
   if (n_iters < 0 || !(bisect_tol > 0) || bisect_max < 1)
-    return fail(c, AMM_EINVAL, "amm_wmmse_step: need n_iters >= 0, bisect_tol > 0, bisect_max >= 1");
-  if (!c->started) return fail(c, AMM_EINVAL, "amm_wmmse_step before amm_warmstart");
+    return fail(c, AMM_EINVAL, std::string(what) + ": need n_iters >= 0, bisect_tol > 0, bisect_max >= 1");
+  if (!c->started) return fail(c, AMM_EINVAL, std::string(what) + " before amm_warmstart");
   if (c->wm_bytes < 0)
-    return fail(c, AMM_EUNSUPPORTED, "amm_wmmse_step: an Nt x Nt system of these sizes does not fit shared memory");
+    return fail(c, AMM_EUNSUPPORTED, std::string(what) + ": an Nt x Nt system of these sizes does not fit shared memory");
   if (n_iters == 0) return AMM_OK;
   amm::IterParams p = base_params(c);
   p.n_iters = n_iters;
   p.mode = amm::kFixed;
-  amm::wmmse_kernel<<<c->batch, amm::kThreads, c->wm_bytes, c->stream>>>(p, (float)bisect_tol, bisect_max);
+  amm::wmmse_kernel<<<c->batch, amm::kThreads, c->wm_bytes, c->stream>>>(p, (float)bisect_tol, bisect_max, eig);
   return check_launch(c, "wmmse_kernel");
+}
+
+extern "C" amm_status amm_wmmse_step(amm_ctx* c, int n_iters, double bisect_tol, int bisect_max) {
+  return wmmse_launch(c, "amm_wmmse_step", n_iters, bisect_tol, bisect_max, 0);
+}
+
+extern "C" amm_status amm_wmmse_step_eig(amm_ctx* c, int n_iters, double bisect_tol, int bisect_max) {
+  return wmmse_launch(c, "amm_wmmse_step_eig", n_iters, bisect_tol, bisect_max, 1);
 }
 
 extern "C" amm_status amm_get_V(const amm_ctx* cc, void* V) {

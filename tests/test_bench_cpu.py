@@ -37,3 +37,15 @@ def test_gap_check_counts_every_instance():
         par = bench.gap_check(pool, got, res, iters=4)
     assert par["checked"] == 2 and par["within_1e-3"] == 1 and par["over_1e-3"] == 1
     assert par["failed"] == 1 and not par["all_pass"]
+
+
+def test_wmmse_worker_is_the_oracle_wmmse_on_rounded_inputs():
+    """The WMMSE workload's CPU leg: the oracle's Algorithm 2 on instance b
+    of the workload, inputs rounded as the GPU receives them, WSR in bits."""
+    b, got = bench._wmmse_worker((3, 2))
+    inst = bench._round32(wl.unrolled_64(n=bench.WMMSE_N, first=3, count=1)[0])
+    V0 = osv.initial_precoder(inst.G0, inst.P)
+    _, hist, _ = osv.wmmse(inst.H, inst.sigma2, inst.alpha, inst.P, inst.K, inst.Nr, inst.d, V0, 2,
+                           tol=1e-4, max_bisect=100)
+    assert b == 3 and got == hist[-1] / np.log(2.0)
+    assert bench._instances("wmmse", 3, 1)[0].dims == (1, 16, 64, 2, 2)

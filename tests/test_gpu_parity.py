@@ -251,16 +251,20 @@ def test_host_pipeline_matches_single_context(prec):
     one.close()
 
 
-@pytest.mark.parametrize("shape", [(1, 4, 8, 2, 2), (2, 2, 6, 2, 1), (1, 6, 24, 4, 2)])
-def test_wmmse_step_matches_oracle(shape):
+@pytest.mark.parametrize("eig", [False, True])
+@pytest.mark.parametrize("shape", [(1, 4, 8, 2, 2), (2, 2, 6, 2, 1), (1, 6, 24, 4, 2), (1, 5, 7, 1, 1),
+                                   (1, 8, 33, 2, 2)])
+def test_wmmse_step_matches_oracle(shape, eig):
     """amm_wmmse_step (Algorithm 2: eq. (9), eq. (10), eq. (12) with
-    bisection to width 1e-4, at most 100 halvings) against the oracle's
-    WMMSE from the same projected V^0."""
+    bisection to width 1e-4, at most 100 halvings; eig: the multiplier and
+    V_k from a Jacobi eigen-decomposition of A_k) against the oracle's
+    WMMSE from the same projected V^0; odd Nt and K d < Nt (a singular A_k,
+    so the bisection runs) included."""
     iters = 12
     insts = small_batch(shape, 6, 7000 + sum(shape))
     g = GpuRun(insts)
     g.warmstart()
-    g.s.wmmse_step(iters, 1e-4, 100)
+    g.s.wmmse_step(iters, 1e-4, 100, eig=eig)
     got = g.wsr()
     assert np.all(g.status() == 0)
     for b, inst in enumerate(insts):
@@ -270,6 +274,26 @@ def test_wmmse_step_matches_oracle(shape):
         want = hist[-1] / np.log(2.0)
         assert abs(got[b] - want) <= WSR_TOL * want, (shape, b, got[b], want)
     g.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 16, 64, 2, 2), (2, 3, 17, 3, 2), (1, 8, 33, 2, 2)])
+def test_wmmse_eig_step_matches_cholesky_step(shape):
+    """One WMMSE iteration from the same V^0: the V update from the Jacobi
+    eigen-decomposition of A_k agrees with the Cholesky-bisection update
+    (the same multiplier to the bisection width, the same V up to FP32
+    rounding of the two factorisations)."""
+    insts = small_batch(shape, 4, 7100 + sum(shape))
+    Vs = []
+    for eig in (False, True):
+        g = GpuRun(insts)
+        g.warmstart()
+        g.s.wmmse_step(1, 1e-6, 100, eig=eig)
+        assert np.all(g.status() == 0)
+        Vs.append(g.V())
+        g.close()
+    for b in range(len(insts)):
+        err = np.linalg.norm(Vs[1][b] - Vs[0][b]) / np.linalg.norm(Vs[0][b])
+        assert err <= 2e-3, (shape, b, err)
 
 
 @pytest.mark.parametrize("solves", [0, 2])

@@ -236,10 +236,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
     for (int q = 0; q < NS; ++q)
       *reinterpret_cast<__nv_bfloat16*>(Ar[q] + tc::kmaj_off(row, k, Kp)) = neg ? __hneg(t[q]) : t[q];
   };
-  // ---- A operands from the normalised channel
+  unsigned phase = 0;  // of mbar: the bulk copy below, then the MMA commits
+  // ---- A operands from the normalised channel, staged into the idle Z
+  //      buffer by the TMA bulk-copy engine (one row per copy) when its
+  //      rows are wide enough
+  const bool h_staged = Nt <= ldz;
+  if (h_staged) stage_rows(Zs, ldz, Hg, Nt, m, Nt, &mbar, phase, p.spin_budget, &s_fail);
   for (int e = tid; e < m * Nt; e += blockDim.x) {
     const int i = e / Nt, q = e - i * Nt;
-    const float2 h = Hg[e];
+    const float2 h = h_staged ? Zs[(long long)i * ldz + q] : Hg[e];
     __nv_bfloat16 rt[3], it[3];
     split(h.x, rt);
     split(h.y, it);
@@ -305,7 +310,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_iterate_kernel(IterParams p, i
       put_B1(cc, v);
     }
   };
-  unsigned phase = 0;
   // the products of the split terms: (a-term, b-term)
   const int npairs = (NS == 1) ? 1 : (NS == 2 ? 3 : 6);
   const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};

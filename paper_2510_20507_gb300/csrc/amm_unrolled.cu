@@ -8,7 +8,8 @@
 // The forward pass keeps (V^{c-1}, V^c) at every ck-th iteration; the
 // backward pass recomputes each segment of ck iterations from its checkpoint
 // and runs the adjoint of the iteration backwards through it.  Complex
-// matrices are FP32; the per-user Nr x Nr / d x d Hermitian solves are FP64.
+// matrices are FP32; the per-user Nr x Nr / d x d Hermitian solves are
+// float-float (pairs of FP32), the log-det FP64.
 //
 // Gradients use the real-gradient convention for complex variables: for a
 // real L and complex X, Xbar = dL/dRe(X) + i dL/dIm(X), so that
@@ -114,61 +115,73 @@ struct UView {
   const float* alpha;
 };
 
-// ---- FP64 helpers on small row-major complex matrices (one thread)
-struct Z64 {
-  double x, y;
+// ---- float-float helpers on small row-major complex matrices (one thread):
+// pairs of FP32 (amm_ff.cuh, about 48 significant bits) on the FP32 pipe,
+// where one warp's chain of FP64 instructions would wait ~64 cycles each
+struct Zc {
+  ff x, y;
 };
-__device__ __forceinline__ Z64 zmk(double x, double y) {
-  Z64 r;
+__device__ __forceinline__ Zc zmk(ff x, ff y) {
+  Zc r;
   r.x = x;
   r.y = y;
   return r;
 }
-__device__ __forceinline__ Z64 zld(float2 v) { return zmk((double)v.x, (double)v.y); }
-__device__ __forceinline__ Z64 zmul(Z64 a, Z64 b) { return zmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ Z64 zcmul(Z64 a, Z64 b) { return zmk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a) b
-__device__ __forceinline__ Z64 zadd(Z64 a, Z64 b) { return zmk(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ Z64 zsub(Z64 a, Z64 b) { return zmk(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 zst(Z64 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ Zc zmkf(float x, float y) { return zmk(ff_from(x), ff_from(y)); }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_half(ff a) { return ff_make(0.5f * a.hi, 0.5f * a.lo); }  // exact
+__device__ __forceinline__ Zc zld(float2 v) { return zmkf(v.x, v.y); }
+__device__ __forceinline__ Zc zmul(Zc a, Zc b) {
+  return zmk(ff_fma(a.x, b.x, ff_neg(ff_mul(a.y, b.y))), ff_fma(a.x, b.y, ff_mul(a.y, b.x)));
+}
+__device__ __forceinline__ Zc zcmul(Zc a, Zc b) {  // conj(a) b
+  return zmk(ff_fma(a.x, b.x, ff_mul(a.y, b.y)), ff_fma(a.x, b.y, ff_neg(ff_mul(a.y, b.x))));
+}
+__device__ __forceinline__ Zc zadd(Zc a, Zc b) { return zmk(ff_add(a.x, b.x), ff_add(a.y, b.y)); }
+__device__ __forceinline__ Zc zsub(Zc a, Zc b) { return zmk(ff_sub(a.x, b.x), ff_sub(a.y, b.y)); }
+__device__ __forceinline__ Zc zscale(Zc a, ff s) { return zmk(ff_mul(a.x, s), ff_mul(a.y, s)); }
+__device__ __forceinline__ float2 zst(Zc a) { return make_float2(a.x.hi, a.y.hi); }  // hi = the value rounded
 
 // Cholesky A = L L^H of an n x n Hermitian matrix (lower triangle of A
-// read); returns false on a non-positive pivot.  iL[j] = 1 / L_jj (one FP64
-// rsqrt per pivot, no division), and the pivots L_jj^2 go to piv[j].
+// read); returns false on a non-positive pivot.  iL[j] = 1 / L_jj (a
+// float-float rsqrt per pivot, no division), and the pivots L_jj^2 go to
+// piv[j].
 template <int n>
-__device__ __forceinline__ bool z_chol(const Z64* A, Z64* L, double* iL, double* piv) {
+__device__ __forceinline__ bool z_chol(const Zc* A, Zc* L, ff* iL, ff* piv) {
 #pragma unroll
   for (int j = 0; j < n; ++j) {
-    double dj = A[j * n + j].x;
-    for (int k = 0; k < j; ++k) dj -= L[j * n + k].x * L[j * n + k].x + L[j * n + k].y * L[j * n + k].y;
-    if (!(dj > 0.0)) return false;
-    const double rj = rsqrt(dj);
+    ff dj = A[j * n + j].x;
+    for (int k = 0; k < j; ++k)
+      dj = ff_sub(dj, ff_fma(L[j * n + k].x, L[j * n + k].x, ff_mul(L[j * n + k].y, L[j * n + k].y)));
+    if (!(dj.hi > 0.f) || !(dj.hi < INFINITY)) return false;
+    const ff rj = ff_rsqrt(dj);
     iL[j] = rj;
     piv[j] = dj;
-    L[j * n + j] = zmk(dj * rj, 0.0);
+    L[j * n + j] = zmk(ff_mul(dj, rj), ff_from(0.f));
     for (int i = j + 1; i < n; ++i) {
-      Z64 s = A[i * n + j];
-      for (int k = 0; k < j; ++k) s = zsub(s, zmul(L[i * n + k], zmk(L[j * n + k].x, -L[j * n + k].y)));
-      L[i * n + j] = zmk(s.x * rj, s.y * rj);
+      Zc s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s = zsub(s, zmul(L[i * n + k], zmk(L[j * n + k].x, ff_neg(L[j * n + k].y))));
+      L[i * n + j] = zscale(s, rj);
     }
-    for (int i = 0; i < j; ++i) L[i * n + j] = zmk(0.0, 0.0);
+    for (int i = 0; i < j; ++i) L[i * n + j] = zmkf(0.f, 0.f);
   }
   return true;
 }
 
 // X = A^{-1} B for A = L L^H (n x n), B n x k, all row-major.
 template <int n, int k>
-__device__ __forceinline__ void z_chol_solve(const Z64* L, const double* iL, const Z64* B, Z64* X) {
+__device__ __forceinline__ void z_chol_solve(const Zc* L, const ff* iL, const Zc* B, Zc* X) {
 #pragma unroll
   for (int c = 0; c < k; ++c) {
     for (int i = 0; i < n; ++i) {  // L y = b
-      Z64 s = B[i * k + c];
+      Zc s = B[i * k + c];
       for (int j = 0; j < i; ++j) s = zsub(s, zmul(L[i * n + j], X[j * k + c]));
-      X[i * k + c] = zmk(s.x * iL[i], s.y * iL[i]);
+      X[i * k + c] = zscale(s, iL[i]);
     }
     for (int i = n - 1; i >= 0; --i) {  // L^H x = y
-      Z64 s = X[i * k + c];
+      Zc s = X[i * k + c];
       for (int j = i + 1; j < n; ++j) s = zsub(s, zcmul(L[j * n + i], X[j * k + c]));
-      X[i * k + c] = zmk(s.x * iL[i], s.y * iL[i]);
+      X[i * k + c] = zscale(s, iL[i]);
     }
   }
 }
@@ -182,39 +195,39 @@ template <int NR, int DD>
 __device__ __noinline__ bool u_solve_user_t(const UView& X, int r, bool stage2, bool want_ld) {
   constexpr int Nr = NR, d = DD;
   const int n = X.n;
-  Z64 A[16], L[16], I4[16], Ti[16], Zo[16], Uu[16], E[16], Le[16], Wm[16];
+  Zc A[16], L[16], I4[16], Ti[16], Zo[16], Uu[16], E[16], Le[16], Wm[16];
   for (int a = 0; a < Nr; ++a)
     for (int b = 0; b < Nr; ++b) {
       A[a * Nr + b] = zld(X.Tc[(r * Nr + a) * Nr + b]);  // FP32 covariance (u_forward_iter)
-      I4[a * Nr + b] = zmk(a == b ? 1.0 : 0.0, 0.0);
+      I4[a * Nr + b] = zmkf(a == b ? 1.f : 0.f, 0.f);
     }
-  double iLt[4], pv[4];
+  ff iLt[4], pv[4];
   if (!z_chol<Nr>(A, L, iLt, pv)) return false;
   z_chol_solve<Nr, Nr>(L, iLt, I4, Ti);
   for (int a = 0; a < Nr; ++a)
     for (int s = 0; s < d; ++s) Zo[a * d + s] = zld(X.Z[(r * Nr + a) * n + r * d + s]);
   for (int a = 0; a < Nr; ++a)
     for (int s = 0; s < d; ++s) {
-      Z64 acc = zmk(0.0, 0.0);
+      Zc acc = zmkf(0.f, 0.f);
       for (int b = 0; b < Nr; ++b) acc = zadd(acc, zmul(Ti[a * Nr + b], Zo[b * d + s]));
       Uu[a * d + s] = acc;
     }
   for (int s = 0; s < d; ++s)
     for (int u = 0; u < d; ++u) {
-      Z64 acc = zmk(s == u ? 1.0 : 0.0, 0.0);
+      Zc acc = zmkf(s == u ? 1.f : 0.f, 0.f);
       for (int a = 0; a < Nr; ++a) acc = zsub(acc, zcmul(Uu[a * d + s], Zo[a * d + u]));
       E[s * d + u] = acc;
     }
   for (int s = 0; s < d; ++s)  // Hermitian part
     for (int u = s; u < d; ++u) {
-      const Z64 h = zmk(0.5 * (E[s * d + u].x + E[u * d + s].x), 0.5 * (E[s * d + u].y - E[u * d + s].y));
+      const Zc h = zmk(ff_half(ff_add(E[s * d + u].x, E[u * d + s].x)), ff_half(ff_sub(E[s * d + u].y, E[u * d + s].y)));
       E[s * d + u] = h;
-      E[u * d + s] = zmk(h.x, -h.y);
+      E[u * d + s] = zmk(h.x, ff_neg(h.y));
     }
-  double iLe[4], pe[4];
+  ff iLe[4], pe[4];
   if (!z_chol<d>(E, Le, iLe, pe)) return false;
   for (int s = 0; s < d; ++s)
-    for (int u = 0; u < d; ++u) I4[s * d + u] = zmk(s == u ? 1.0 : 0.0, 0.0);
+    for (int u = 0; u < d; ++u) I4[s * d + u] = zmkf(s == u ? 1.f : 0.f, 0.f);
   if (stage2) {
     z_chol_solve<d, d>(Le, iLe, I4, Wm);
   } else {
@@ -225,14 +238,14 @@ __device__ __noinline__ bool u_solve_user_t(const UView& X, int r, bool stage2, 
   for (int q = 0; q < d * d; ++q) X.W[r * d * d + q] = zst(Wm[q]);
   for (int a = 0; a < Nr; ++a)
     for (int s = 0; s < d; ++s) {
-      Z64 acc = zmk(0.0, 0.0);
+      Zc acc = zmkf(0.f, 0.f);
       for (int u = 0; u < d; ++u) acc = zadd(acc, zmul(Uu[a * d + u], Wm[u * d + s]));
       X.P[(r * Nr + a) * d + s] = zst(acc);
     }
-  if (want_ld) {  // log det E_r from the pivots, only where the WSR is read
-    double prod = 1.0;
-    for (int j = 0; j < d; ++j) prod *= pe[j];
-    X.ld[r] = log(prod);
+  if (want_ld) {  // log det E_r from the pivots, only where the WSR is read (one FP64 log)
+    ff prod = ff_from(1.f);
+    for (int j = 0; j < d; ++j) prod = ff_mul(prod, pe[j]);
+    X.ld[r] = log(ff_to_double(prod));
   }
   return true;
 }
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(kUThreads) u_forward_kernel(UParams p) {
 // 2 alpha P^H Ybar, Ubar, Pbar and Zhbar = U Abar over the columns, then the
 // adjoints of P = U W, W = E^{-1}, E = I - U^H Zo, U = T^{-1} Zo and
 // T = I + Z Z^H, giving Zbar_r.  N_r and d are compile-time, so the small
-// FP64 matrices live in registers.
+// matrices live in registers.
 template <int NR, int DD>
 __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2, const float2* Yb, float2* Zhb,
                                                  float2* Zb, float2* Ub, float2* Pb) {
@@ -446,8 +459,8 @@ __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2
       Zhb[(r * Nr + a) * n + c] = zhb;
     }
   }
-  // From here FP32: products of the small matrices that the FP64 forward
-  // solve produced (no factorisation).  P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
+  // From here FP32: products of the small matrices that the float-float
+  // forward solve produced (no factorisation).  P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
   float2 Ubr[16], Wb[16], Uu[16], Wm[16], Eb[16], Bm[16], Tb[16], Ti[16];
   for (int q = 0; q < Nr * d; ++q) Uu[q] = X.U[r * Nr * d + q];
   for (int q = 0; q < d * d; ++q) Wm[q] = X.W[r * d * d + q];

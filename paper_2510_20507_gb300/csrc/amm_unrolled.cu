@@ -608,35 +608,69 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
   // per user: Abar = 2 alpha P^H Ybar, Ubar, Pbar, Zhbar = U Abar; then W, E and T
   for (int r = threadIdx.x; r < K; r += blockDim.x) u_adjoint_user(X, r, stage2, Yb, Zhb, Zb, Ub, Pb);
   __syncthreads();
-  // Hbar += Y Gbar^H + Zhbar Vhat^H + Zbar Va^H  (Gbar = -gam B).  Lanes hold
-  // consecutive q, so rows q n of B, Vhat, Va are read with stride n; each
-  // lane starts its column sweep at its own offset (bank_rot).
-  const int rot = bank_rot(n);
-  for (int e = threadIdx.x; e < m * Nt; e += blockDim.x) {
-    const int i = e / Nt, q = e - i * Nt;
-    float2 acc = Hb[e];
-    for (int k = 0; k < n; ++k) {
-      const int c = (k + rot < n) ? k + rot : k + rot - n;
-      const float2 gbar = cscale(B[q * n + c], -gam);
-      acc = cfma(X.Y[i * n + c], make_float2(gbar.x, -gbar.y), acc);
-      acc = cfma(Zhb[i * n + c], make_float2(Vh[q * n + c].x, -Vh[q * n + c].y), acc);
-      acc = cfma(Zb[i * n + c], make_float2(Va[q * n + c].x, -Va[q * n + c].y), acc);
+  // Hbar += Y Gbar^H + Zhbar Vhat^H + Zbar Va^H  (Gbar = -gam B): a sum over
+  // 3 n products per entry, 2 x 4 entries per thread (rows i0 + a ntr,
+  // columns q0 + b ntc), the 3 x 6 operand values of a column loaded once
+  // for the 24 products.  Rows q n of B, Vhat, Va are n apart, so each lane
+  // starts its column sweep at its own offset (bank_rot).
+  {
+    const int rot = bank_rot(n);
+    constexpr int TM = 2, TN = 4;
+    const int ntr = (m + TM - 1) / TM, ntc = (Nt + TN - 1) / TN;
+    for (int tile = threadIdx.x; tile < ntr * ntc; tile += blockDim.x) {
+      const int tr = tile / ntc, tq = tile - tr * ntc;
+      int ii[TM], qq[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) ii[a] = min(tr + a * ntr, m - 1);
+#pragma unroll
+      for (int bq = 0; bq < TN; ++bq) qq[bq] = min(tq + bq * ntc, Nt - 1);
+      float2 acc[TM][TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int bq = 0; bq < TN; ++bq) acc[a][bq] = make_float2(0.f, 0.f);
+      for (int k = 0; k < n; ++k) {
+        const int c = (k + rot < n) ? k + rot : k + rot - n;
+        float2 y[TM], zh[TM], zb[TM], g[TN], vh[TN], va[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+          y[a] = X.Y[ii[a] * n + c];
+          zh[a] = Zhb[ii[a] * n + c];
+          zb[a] = Zb[ii[a] * n + c];
+        }
+#pragma unroll
+        for (int bq = 0; bq < TN; ++bq) {
+          const float2 gb = cscale(B[qq[bq] * n + c], -gam);
+          g[bq] = make_float2(gb.x, -gb.y);
+          vh[bq] = make_float2(Vh[qq[bq] * n + c].x, -Vh[qq[bq] * n + c].y);
+          va[bq] = make_float2(Va[qq[bq] * n + c].x, -Va[qq[bq] * n + c].y);
+        }
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int bq = 0; bq < TN; ++bq)
+            acc[a][bq] = cfma(zb[a], va[bq], cfma(zh[a], vh[bq], cfma(y[a], g[bq], acc[a][bq])));
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int bq = 0; bq < TN; ++bq) {
+          const int i = tr + a * ntr, q = tq + bq * ntc;
+          if (i < m && q < Nt) Hb[i * Nt + q] = cadd(Hb[i * Nt + q], acc[a][bq]);
+        }
     }
-    Hb[e] = acc;
   }
   __syncthreads();
   // Vhat-bar = B + H^H Zhbar (in B);  A2 += H^H Zbar + (1 + w) Vhat-bar;  A3 = -w Vhat-bar
-  for (int e = threadIdx.x; e < N; e += blockDim.x) {
-    const int q = e / n, c = e - q * n;
-    float2 vhb = B[e], zz = make_float2(0.f, 0.f);
-    for (int i = 0; i < m; ++i) {
-      const float2 hc = make_float2(X.H[i * Nt + q].x, -X.H[i * Nt + q].y);
-      vhb = cfma(hc, Zhb[i * n + c], vhb);
-      zz = cfma(hc, Zb[i * n + c], zz);
-    }
+  block_cgemm_tiled<1>(gemm_tile_for(0, Nt, n), Nt, n, m, X.H, Nt, Zhb, n,
+                       [&](int q, int c, float2 v) { B[q * n + c] = cadd(B[q * n + c], v); });
+  __syncthreads();
+  block_cgemm_tiled<1>(gemm_tile_for(0, Nt, n), Nt, n, m, X.H, Nt, Zb, n, [&](int q, int c, float2 zz) {
+    const int e = q * n + c;
+    const float2 vhb = B[e];
     A2[e] = make_float2(A2[e].x + zz.x + (1.f + omega) * vhb.x, A2[e].y + zz.y + (1.f + omega) * vhb.y);
     A3[e] = make_float2(-omega * vhb.x, -omega * vhb.y);
-  }
+  });
   __syncthreads();
 }
 

@@ -420,8 +420,9 @@ __global__ void __launch_bounds__(kUThreads) u_forward_kernel(UParams p) {
   }
 }
 
-// Per-user part of the adjoint of one iteration (thread r < K): Abar =
-// 2 alpha P^H Ybar, Ubar, Pbar and Zhbar = U Abar over the columns, then the
+// Per-user part of the adjoint of one iteration (one warp per user r, its
+// lanes over the columns): Abar = 2 alpha P^H Ybar, Ubar, Pbar (summed over
+// the lanes) and Zhbar = U Abar over the columns, then (every lane) the
 // adjoints of P = U W, W = E^{-1}, E = I - U^H Zo, U = T^{-1} Zo and
 // T = I + Z Z^H, giving Zbar_r.  N_r and d are compile-time, so the small
 // matrices live in registers.
@@ -429,35 +430,49 @@ template <int NR, int DD>
 __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2, const float2* Yb, float2* Zhb,
                                                  float2* Zb, float2* Ub, float2* Pb) {
   constexpr int Nr = NR, d = DD;
-  const int n = X.n;
+  const int n = X.n, lane = threadIdx.x & 31;
   const float a2 = 2.f * X.alpha[r];
-  float2 ub[16], pb[16];
-  for (int q = 0; q < Nr * d; ++q) ub[q] = pb[q] = make_float2(0.f, 0.f);
-  const int rot = bank_rot(n);  // lanes hold users: rows r Nr n .. are read with stride Nr n
-  for (int k = 0; k < n; ++k) {
-    const int c = (k + rot < n) ? k + rot : k + rot - n;
+  float2 ub[16], pb[16], Ur[16], Pr[16];
+#pragma unroll
+  for (int q = 0; q < Nr * d; ++q) {
+    ub[q] = pb[q] = make_float2(0.f, 0.f);
+    Ur[q] = X.U[r * Nr * d + q];
+    Pr[q] = X.P[r * Nr * d + q];
+  }
+  // the warp's lanes take the columns: A = U^H Zh - S, Abar = 2 alpha P^H Ybar
+  for (int c = lane; c < n; c += 32) {
     float2 As[kMaxNr], Ab[kMaxNr];
+#pragma unroll
     for (int s2 = 0; s2 < d; ++s2) {
       float2 acc = make_float2(c == r * d + s2 ? -1.f : 0.f, 0.f);
       float2 acb = make_float2(0.f, 0.f);
+#pragma unroll
       for (int a = 0; a < Nr; ++a) {
-        acc = cjfma(X.U[(r * Nr + a) * d + s2], X.Zh[(r * Nr + a) * n + c], acc);
-        acb = cjfma(X.P[(r * Nr + a) * d + s2], Yb[(r * Nr + a) * n + c], acb);
+        acc = cjfma(Ur[a * d + s2], X.Zh[(r * Nr + a) * n + c], acc);
+        acb = cjfma(Pr[a * d + s2], Yb[(r * Nr + a) * n + c], acb);
       }
       As[s2] = acc;
       Ab[s2] = cscale(acb, a2);
     }
+#pragma unroll
     for (int a = 0; a < Nr; ++a) {
       const float2 zh = X.Zh[(r * Nr + a) * n + c], yb = Yb[(r * Nr + a) * n + c];
       float2 zhb = make_float2(0.f, 0.f);
+#pragma unroll
       for (int s2 = 0; s2 < d; ++s2) {
         // Ubar += Zh Abar^H;  Pbar += 2 alpha Ybar A^H;  Zhbar = U Abar
         ub[a * d + s2] = cfma(zh, make_float2(Ab[s2].x, -Ab[s2].y), ub[a * d + s2]);
         pb[a * d + s2] = cfma(cscale(yb, a2), make_float2(As[s2].x, -As[s2].y), pb[a * d + s2]);
-        zhb = cfma(X.U[(r * Nr + a) * d + s2], Ab[s2], zhb);
+        zhb = cfma(Ur[a * d + s2], Ab[s2], zhb);
       }
       Zhb[(r * Nr + a) * n + c] = zhb;
     }
+  }
+  // the column sums of Ubar and Pbar over the lanes; every lane holds them
+#pragma unroll
+  for (int q = 0; q < Nr * d; ++q) {
+    ub[q] = warp_sum(ub[q]);
+    pb[q] = warp_sum(pb[q]);
   }
   // From here FP32: products of the small matrices that the float-float
   // forward solve produced (no factorisation).  P = U W: Ubar += Pbar W^H, Wbar = U^H Pbar
@@ -529,8 +544,7 @@ __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2
       for (int u = 0; u < d; ++u) acc = csub(acc, cmul(Uu[a * d + u], Eb[u * d + s2]));
       ownb[a * d + s2] = acc;
     }
-  for (int k = 0; k < n; ++k) {
-    const int c = (k + rot < n) ? k + rot : k + rot - n;
+  for (int c = lane; c < n; c += 32) {
     const bool own = c >= r * d && c < r * d + d;
     for (int a = 0; a < Nr; ++a) {
       float2 acc = make_float2(0.f, 0.f);
@@ -542,10 +556,11 @@ __device__ __noinline__ void u_adjoint_user_t(const UView& X, int r, bool stage2
       Zb[(r * Nr + a) * n + c] = acc;
     }
   }
-  for (int q = 0; q < Nr * d; ++q) {
-    Ub[r * Nr * d + q] = Ubr[q];
-    Pb[r * Nr * d + q] = pb[q];
-  }
+  if (lane == 0)
+    for (int q = 0; q < Nr * d; ++q) {
+      Ub[r * Nr * d + q] = Ubr[q];
+      Pb[r * Nr * d + q] = pb[q];
+    }
 }
 
 __device__ __forceinline__ void u_adjoint_user(const UView& X, int r, bool stage2, const float2* Yb, float2* Zhb,
@@ -606,7 +621,8 @@ __device__ void u_adjoint_iter(const UParams& p, const UView& X, const ULayout& 
                        [&](int r, int c, float2 v) { Yb[r * n + c] = cscale(v, -gam); });
   __syncthreads();
   // per user: Abar = 2 alpha P^H Ybar, Ubar, Pbar, Zhbar = U Abar; then W, E and T
-  for (int r = threadIdx.x; r < K; r += blockDim.x) u_adjoint_user(X, r, stage2, Yb, Zhb, Zb, Ub, Pb);
+  // one warp per user (lanes over the columns)
+  for (int r = threadIdx.x >> 5; r < K; r += blockDim.x >> 5) u_adjoint_user(X, r, stage2, Yb, Zhb, Zb, Ub, Pb);
   __syncthreads();
   // Hbar += Y Gbar^H + Zhbar Vhat^H + Zbar Va^H  (Gbar = -gam B): a sum over
   // 3 n products per entry, 2 x 4 entries per thread (rows i0 + a ntr,

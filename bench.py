@@ -229,11 +229,35 @@ def _oracle_serial(jobs):
     return [x for j in jobs for x in _oracle_worker(j)]
 
 
+def _pool_init(barrier):
+    """Worker start-up: import what the oracle workers use, then wait until
+    every worker has done so (a worker that starts later gives up waiting
+    after a minute)."""
+    import threading
+    import numpy  # noqa: F401
+    from oracle import parity  # noqa: F401
+    import workloads  # noqa: F401
+    try:
+        barrier.wait(timeout=60)
+    except threading.BrokenBarrierError:
+        pass
+
+
 def make_pool(cores):
+    """A spawn pool of oracle workers (spawned before the first CUDA call),
+    returned once every worker has finished its imports, so that no worker
+    is still importing on a host core while the GPU is timed."""
     import multiprocessing as mp
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
-    return mp.get_context("spawn").Pool(cores)
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores + 1)
+    pool = ctx.Pool(cores, initializer=_pool_init, initargs=(barrier,))
+    try:
+        barrier.wait(timeout=600)
+    except Exception:
+        pass
+    return pool
 
 
 def oracle_solve(pool, indices):

@@ -56,13 +56,13 @@ def algorithmic_gemm_flops(C, K, Nt, Nr, d):
 # grows with the instance count, so a full launch is this times its
 # instances).  Valid only for the kernel sources the captures ran: see
 # kernel_digest().  Kernels without an entry report null.
-TRAFFIC = {"digest": "3108108a3dea24c8",
-           "tc_iterate_kernel": (484.864512e6 + 283.674112e6) / 4864,
-           "cluster_iterate_kernel": (186.311680e6 + 47.567104e6) / 160}
+TRAFFIC = {"digest": "57f30d916a58a20f",
+           "tc_iterate_kernel": (486.432256e6 + 283.902976e6) / 4864,
+           "cluster_iterate_kernel": (186.953984e6 + 47.981568e6) / 160}
 # pipe utilisation of the same captures (% of peak, ncu --set full), reported
 # beside the roofline while the sources match the digest: which unit is busy
-PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.80, "fp64_pct": 0.34, "fma_pct": 19.14, "alu_pct": 23.25,
-                               "dram_pct": 0.22, "issue_active_pct": 37.96},
+PIPES = {"tc_iterate_kernel": {"tensor_pct": 5.78, "fp64_pct": 0.34, "fma_pct": 19.09, "alu_pct": 23.19,
+                               "dram_pct": 0.22, "issue_active_pct": 37.85},
          "cluster_iterate_kernel": {"tensor_pct": 0.0, "fp64_pct": 0.28, "fma_pct": 30.31, "alu_pct": 16.21,
                                     "dram_pct": 0.10, "issue_active_pct": 45.62}}
 

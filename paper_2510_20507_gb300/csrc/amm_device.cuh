@@ -1,6 +1,7 @@
 // Device routines shared by the solver kernels: block-wide complex GEMM,
-// TMA bulk staging, the FP64 per-user Hermitian solves and the Lanczos
-// estimate of ||F_k||_2.  Included by each kernel translation unit.
+// TMA bulk staging, the compensated covariance, the per-user Hermitian
+// solves (FP64, float-float or FP32) and the Lanczos estimate of
+// ||F_k||_2.  Included by each kernel translation unit.
 #pragma once
 
 #include <math.h>

@@ -185,7 +185,8 @@ __device__ __forceinline__ void iterate_instance(const IterParams& p, int b, uns
     // ---- S3a: interference-plus-noise covariance Q_r (upper triangle), sigma^2 = 1
     covariance_phase(D, Ly, [&](int row, int c) { return Zc[(long long)row * ldz + c]; }, sQ);
     __syncthreads();
-    // ---- S3b/S4: FP64 small solves, one thread per user; rho = WSR(V^{t-1})
+    // ---- S3b/S4: the small solves (FP64, float-float or FP32; eight or four
+    //      lanes per user); rho = WSR(V^{t-1})
     const bool want_rate = need_rate(s_ctrl[1], p.mode, it, n_iters);
     solve_phase<T>(D, Ly, Zc, ldz, sQ, sU, sUW, sRho, alpha_u, p.mode != kEvalWsr, want_rate, red, &s_fail);
     if (s_fail != kOk) break;

@@ -27,6 +27,7 @@ def header_functions():
 def test_header_declares_entry_points():
     names = header_functions()
     for must in ["amm_create", "amm_warmstart", "amm_step", "amm_solve", "amm_wsr", "amm_wmmse_step",
+                 "amm_wmmse_step_eig",
                  "amm_set_problem", "amm_get_state", "amm_set_state", "amm_destroy"]:
         assert must in names
 
@@ -86,6 +87,8 @@ def test_null_context_is_rejected(lib):
     import paper_2510_20507_gb300 as pkg
     assert lib.amm_step(None, 1) == pkg.AMM_EINVAL
     assert lib.amm_wsr(None, None) == pkg.AMM_EINVAL
+    assert lib.amm_wmmse_step(None, 1, 1e-4, 100) == pkg.AMM_EINVAL
+    assert lib.amm_wmmse_step_eig(None, 1, 1e-4, 100) == pkg.AMM_EINVAL
     lib.amm_destroy(None)
 
 
